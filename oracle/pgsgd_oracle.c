@@ -1,0 +1,720 @@
+/*
+ * CPU oracle for path-guided SGD pangenome layout (PG-SGD) and its path-stress
+ * metrics, after "Rapid GPU-Based Pangenome Graph Layout" (SC24).
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is a plain, slow, sequential restatement
+ * of the method used to check the CUDA library. Only the tests, the smoke
+ * check and the benchmark's CPU-baseline leg may load it. It shares no code,
+ * header or table with the CUDA library: both follow the same written sampler
+ * definition and each implements it on its own.
+ *
+ * What is here, by the passage it follows:
+ *   - Algorithm 1 (Section II-C): the outer loop over iterations with learning
+ *     rate eta = S[iter], the inner loop of N_steps = 10 * sum |p| updates,
+ *     path choice proportional to |p|, the cooling switch (iter >= N_iters / 2
+ *     or a coin), the power-law / uniform choice of the second node, the coin
+ *     for each visualization point, the pair stress and the update of both
+ *     points. The update is the one of Zheng et al. that the paper adopts
+ *     (Section II-C, Fig. 3): w = d^-2, mu = min(eta w, 1),
+ *     r = mu (|v_i - v_j| - d) / (2 |v_i - v_j|), v_i -= r (v_i - v_j),
+ *     v_j += r (v_i - v_j).
+ *   - Hogwild! execution of the inner loop (Section III-A): the optional
+ *     threaded mode runs the inner loop on several threads with unsynchronised
+ *     (relaxed atomic) loads and stores of the coordinates. One thread gives
+ *     the sequential definition.
+ *   - Eq. 1 (Section V-A): path stress, every same-path node pair averaged over
+ *     its four endpoint combinations.
+ *   - Eq. 2 (Section V-B): sampled path stress over 100 |p| pairs per path and
+ *     its 95 % confidence interval mu +- 1.96 sigma / sqrt(n), sigma from a
+ *     second pass over the same samples.
+ *
+ * Readings where the paper is silent (each one is listed in the design notes):
+ *   - Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key
+ *     (seed_lo, seed_hi). Update u of iteration t uses counter
+ *     (u_lo, u_hi, t, b) for block b = 0, 1, ...; words w0..w3 come from block
+ *     0, w4..w7 from block 1 and so on. Stress sample q of path p uses counter
+ *     (q_lo, q_hi, 0x80000000 | p, b) under the stress seed.
+ *   - Step i: g = mulhi64(w0 | w1 << 32, S); p is the path whose step range
+ *     holds g; i = g - off[p]. This is "p with probability |p| / S, then i
+ *     uniform in p". Paths with fewer than two steps give no update.
+ *   - cooling = (2 t >= T) or (w2 & 1).
+ *   - Power law: k follows Zipf(theta) on [1, n_p - 1], drawn by
+ *     rejection-inversion (Hoermann and Derflinger, ACM TOMACS 6(3), 1996)
+ *     evaluated in IEEE binary32 with the operation order fixed below (no
+ *     fused multiply-add anywhere; a draw with k >= 256 is accepted without
+ *     the rejection test), one 32-bit word per trial: w4, w5, w6, w7,
+ *     then block 2, and so on, at most 64 trials (then k = 1). Direction bit
+ *     (w2 >> 1) & 1: 1 = forward (j = i + k), 0 = backward (j = i - k); if that
+ *     leaves the path the other direction is used; if both leave it, j is the
+ *     path end farther from i.
+ *   - Uniform: x = mulhi64(w4 | w5 << 32, n_p - 1); j = x + (x >= i).
+ *   - Endpoint bits e_i = (w2 >> 2) & 1, e_j = (w2 >> 3) & 1, 0 = start point,
+ *     1 = end point. A step entered in reverse orientation meets the node's end
+ *     first, so the endpoint's path position is pos + ((e ^ rev) ? len : 0).
+ *     d_ref = |ep_i - ep_j| in exact integers; d_ref = 0 gives no update.
+ *   - |v_i - v_j| = 0 gives no update (no direction to move along).
+ *   - Learning rate: eta_t = eta_max exp(-lambda t), lambda =
+ *     ln(eta_max / eta_min) / (T - 1) (the annealing of Zheng et al.).
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10, from the definition in Salmon et al. (SC'11), Sec. 4. */
+/* ------------------------------------------------------------------ */
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t prod_a = (uint64_t)0xD2511F53u * x0; /* multiplier M0 on word 0 */
+        uint64_t prod_b = (uint64_t)0xCD9E8D57u * x2; /* multiplier M1 on word 2 */
+        uint32_t hi_a = (uint32_t)(prod_a >> 32), lo_a = (uint32_t)prod_a;
+        uint32_t hi_b = (uint32_t)(prod_b >> 32), lo_b = (uint32_t)prod_b;
+        uint32_t y0 = hi_b ^ x1 ^ k0;
+        uint32_t y1 = lo_b;
+        uint32_t y2 = hi_a ^ x3 ^ k1;
+        uint32_t y3 = lo_a;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+        k0 += 0x9E3779B9u; /* Weyl key schedule */
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+static void philox_block(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
+                         uint32_t c3, uint32_t out[4])
+{
+    uint32_t ctr[4] = {c0, c1, c2, c3};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    orc_philox4x32_10(ctr, key, out);
+}
+
+/* Upper 64 bits of the 128-bit product: maps a uniform 64-bit word onto [0, n). */
+static uint64_t mulhi64(uint64_t a, uint64_t b)
+{
+    return (uint64_t)(((unsigned __int128)a * b) >> 64);
+}
+
+/* ------------------------------------------------------------------ */
+/* binary32 elementary functions with a fixed operation order.         */
+/* ln: x = 2^e m, m in [sqrt(1/2), sqrt(2)); ln m = 2 atanh(s) with     */
+/* s = (m - 1) / (m + 1), as the odd series 2 s (1 + z/3 + ... + z^5/11)*/
+/* in z = s^2. exp: y = n ln2 + r with ln2 split in two parts (Cody and */
+/* Waite), e^r by its Taylor polynomial of degree 7, then times 2^n.    */
+/* ------------------------------------------------------------------ */
+
+static const float LN2_HI = 0x1.62e4p-1f;      /* ln 2 rounded to 15 bits */
+static const float LN2_LO = 0x1.7f7d1cp-20f;   /* ln 2 - LN2_HI */
+static const float INV_LN2 = 0x1.715476p+0f;
+static const float SQRT2 = 0x1.6a09e6p+0f;
+
+static float fbits(uint32_t u) { float f; memcpy(&f, &u, 4); return f; }
+static uint32_t ubits(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
+
+float orc_ln_f32(float x)
+{
+    uint32_t b = ubits(x);
+    int e = (int)((b >> 23) & 0xffu) - 127;
+    float m = fbits((b & 0x7fffffu) | 0x3f800000u);
+    if (m > SQRT2) { m = m * 0.5f; e = e + 1; }
+    float f = m - 1.0f;
+    float s = f / (2.0f + f);
+    float z = s * s;
+    float p = 0x1.745d18p-4f;          /* 1/11 */
+    p = p * z; p = p + 0x1.c71c72p-4f; /* 1/9 */
+    p = p * z; p = p + 0x1.24924ap-3f; /* 1/7 */
+    p = p * z; p = p + 0x1.99999ap-3f; /* 1/5 */
+    p = p * z; p = p + 0x1.555556p-2f; /* 1/3 */
+    p = p * z; p = p + 1.0f;
+    float two_s = s + s;
+    float lnm = two_s * p;
+    float fe = (float)e;
+    float lo = fe * LN2_LO;
+    lo = lo + lnm;
+    float hi = fe * LN2_HI;
+    return hi + lo;
+}
+
+float orc_exp_f32(float y)
+{
+    float t = y * INV_LN2;
+    t = t + 0.5f;
+    int n = (int)floorf(t);
+    float fn = (float)n;
+    float a = fn * LN2_HI;
+    float r = y - a;
+    float c = fn * LN2_LO;
+    r = r - c;
+    float p = 0x1.a01a02p-13f;         /* 1/7! */
+    p = p * r; p = p + 0x1.6c16c2p-10f; /* 1/6! */
+    p = p * r; p = p + 0x1.111112p-7f;  /* 1/5! */
+    p = p * r; p = p + 0x1.555556p-5f;  /* 1/4! */
+    p = p * r; p = p + 0x1.555556p-3f;  /* 1/3! */
+    p = p * r; p = p + 0.5f;
+    p = p * r; p = p + 1.0f;
+    p = p * r; p = p + 1.0f;
+    float scale = fbits((uint32_t)(n + 127) << 23);
+    return p * scale;
+}
+
+/* phi(t) = (e^t - 1) / t, Taylor polynomial to t^8 for |t| < 1/2. */
+static float phi_f32(float t)
+{
+    if (fabsf(t) < 0.5f) {
+        float p = 0x1.71de3ap-19f;          /* 1/9! */
+        p = p * t; p = p + 0x1.a01a02p-16f; /* 1/8! */
+        p = p * t; p = p + 0x1.a01a02p-13f; /* 1/7! */
+        p = p * t; p = p + 0x1.6c16c2p-10f; /* 1/6! */
+        p = p * t; p = p + 0x1.111112p-7f;  /* 1/5! */
+        p = p * t; p = p + 0x1.555556p-5f;  /* 1/4! */
+        p = p * t; p = p + 0x1.555556p-3f;  /* 1/3! */
+        p = p * t; p = p + 0.5f;
+        p = p * t; p = p + 1.0f;
+        return p;
+    }
+    float e = orc_exp_f32(t);
+    e = e - 1.0f;
+    return e / t;
+}
+
+/* psi(t) = ln(1 + t) / t, alternating series to t^11 for |t| < 1/4. */
+static float psi_f32(float t)
+{
+    if (fabsf(t) < 0.25f) {
+        float p = -0x1.555556p-4f;           /* -1/12 */
+        p = p * t; p = p + 0x1.745d18p-4f;   /*  1/11 */
+        p = p * t; p = p + -0x1.99999ap-4f;  /* -1/10 */
+        p = p * t; p = p + 0x1.c71c72p-4f;   /*  1/9 */
+        p = p * t; p = p + -0.125f;          /* -1/8 */
+        p = p * t; p = p + 0x1.24924ap-3f;   /*  1/7 */
+        p = p * t; p = p + -0x1.555556p-3f;  /* -1/6 */
+        p = p * t; p = p + 0x1.99999ap-3f;   /*  1/5 */
+        p = p * t; p = p + -0.25f;           /* -1/4 */
+        p = p * t; p = p + 0x1.555556p-2f;   /*  1/3 */
+        p = p * t; p = p + -0.5f;            /* -1/2 */
+        p = p * t; p = p + 1.0f;
+        return p;
+    }
+    float one_t = 1.0f + t;
+    return orc_ln_f32(one_t) / t;
+}
+
+/* Zipf(theta) on [1, N] by rejection-inversion. h(x) = x^-theta is the      */
+/* unnormalised mass extended to reals, H its antiderivative with H(1) = 0. */
+/* H(x) = ln x * phi((1-theta) ln x); H^-1(y) = exp(y * psi((1-theta) y)).  */
+typedef struct { float theta, omt, A, B, s; uint64_t N; } zipf_t;
+
+static float zipf_H(float x, float omt)
+{
+    float L = orc_ln_f32(x);
+    float t = omt * L;
+    return L * phi_f32(t);
+}
+
+static float zipf_Hinv(float y, float omt)
+{
+    float t = omt * y;
+    float q = psi_f32(t);
+    float a = y * q;
+    return orc_exp_f32(a);
+}
+
+static float zipf_h(float x, float theta)
+{
+    float L = orc_ln_f32(x);
+    float a = theta * L;
+    return orc_exp_f32(-a);
+}
+
+static zipf_t zipf_setup(double theta_d, uint64_t N)
+{
+    zipf_t z;
+    z.theta = (float)theta_d;
+    z.omt = 1.0f - z.theta;
+    z.N = N;
+    z.A = zipf_H(1.5f, z.omt) - 1.0f;           /* H(3/2) - h(1) */
+    float xN = (float)N;
+    xN = xN + 0.5f;
+    z.B = zipf_H(xN, z.omt);                    /* H(N + 1/2) */
+    float h2 = zipf_H(2.5f, z.omt);
+    float hh = zipf_h(2.0f, z.theta);
+    h2 = h2 - hh;
+    z.s = 2.0f - zipf_Hinv(h2, z.omt);          /* squeeze constant */
+    return z;
+}
+
+void orc_zipf_consts(double theta, uint64_t N, float out[3])
+{
+    zipf_t z = zipf_setup(theta, N);
+    out[0] = z.A; out[1] = z.B; out[2] = z.s;
+}
+
+/* One trial with the 32-bit word w: returns 1 and sets *k on acceptance.   */
+/* A draw with k >= 256 is accepted without the test: the exact rejection    */
+/* chance there is below theta (theta + 1) / (24 * 256^2) of h(k), while in   */
+/* binary32 the rounding of H near k is larger than h(k) itself, so the test */
+/* would reject by rounding rather than by the method.                      */
+static int zipf_trial(const zipf_t *z, uint32_t w, uint64_t *k_out)
+{
+    float U = (float)(w >> 8) * 0x1p-24f;
+    float d = z->A - z->B;
+    float t = U * d;
+    float u = z->B + t;
+    float x = zipf_Hinv(u, z->omt);
+    float xr = x + 0.5f;
+    float kf = floorf(xr);
+    uint64_t k = kf < 1.0f ? 1u : (uint64_t)kf;
+    if (k > z->N) k = z->N;
+    if (k >= 256u) { *k_out = k; return 1; }
+    float fk = (float)k;
+    float diff = fk - x;
+    if (diff <= z->s) { *k_out = k; return 1; }
+    float kh = fk + 0.5f;
+    float Hk = zipf_H(kh, z->omt);
+    float hk = zipf_h(fk, z->theta);
+    Hk = Hk - hk;
+    if (u >= Hk) { *k_out = k; return 1; }
+    return 0;
+}
+
+/* Draw k using the words of blocks 1, 2, ... of a Philox counter stream.   */
+/* blk1 holds the words of block 1; (c0, c1, c2) is the counter prefix.      */
+static uint64_t zipf_draw(const zipf_t *z, const uint32_t blk1[4], uint64_t seed,
+                          uint32_t c0, uint32_t c1, uint32_t c2)
+{
+    uint64_t k;
+    for (int m = 0; m < 4; ++m)
+        if (zipf_trial(z, blk1[m], &k)) return k;
+    for (int m = 4; m < 64; ++m) {
+        uint32_t w[4];
+        philox_block(seed, c0, c1, c2, (uint32_t)(2 + (m - 4) / 4), w);
+        if (zipf_trial(z, w[(m - 4) % 4], &k)) return k;
+    }
+    return 1;
+}
+
+/* Test helper: count Zipf(theta) draws on [1, N] keyed by (q, 0x40000000). */
+void orc_zipf_sample(double theta, uint64_t N, uint64_t seed, uint64_t count, uint64_t *out)
+{
+    zipf_t z = zipf_setup(theta, N);
+    for (uint64_t q = 0; q < count; ++q) {
+        uint32_t w[4];
+        philox_block(seed, (uint32_t)q, (uint32_t)(q >> 32), 0x40000000u, 1u, w);
+        out[q] = zipf_draw(&z, w, seed, (uint32_t)q, (uint32_t)(q >> 32), 0x40000000u);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Graph view and the per-update sampler (Algorithm 1, lines 5-13).    */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    uint32_t n_nodes, n_paths;
+    const uint32_t *node_len;
+    const uint64_t *path_off;
+    const uint32_t *step_node;
+    const uint8_t *step_rev;
+    const int64_t *step_pos;
+} orc_graph;
+
+typedef struct {
+    uint64_t g, i, j;
+    int64_t d_ref;
+    uint32_t path;
+    uint8_t cooling, e_i, e_j, skip; /* skip: 0 valid, 1 path < 2 steps, 2 d_ref = 0 */
+} orc_sample_rec;
+
+typedef struct {
+    const orc_graph *G;
+    uint64_t seed;
+    uint32_t T;
+    zipf_t *zipf; /* per path, valid for n_p >= 2 */
+} sampler_t;
+
+static uint32_t find_path(const orc_graph *G, uint64_t g)
+{
+    /* largest p with off[p] <= g; paths with no steps never contain g */
+    uint32_t lo = 0, hi = G->n_paths; /* off[lo] <= g < off[hi] */
+    while (hi - lo > 1) {
+        uint32_t mid = lo + (hi - lo) / 2;
+        if (G->path_off[mid] <= g) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+static int64_t endpoint_pos(const orc_graph *G, uint64_t step, int e)
+{
+    int64_t pos = G->step_pos[step];
+    int rev = G->step_rev[step];
+    int64_t len = G->node_len[G->step_node[step]];
+    return pos + (((e ^ rev) & 1) ? len : 0);
+}
+
+static void sample_update(const sampler_t *S, uint32_t t, uint64_t u, orc_sample_rec *r)
+{
+    const orc_graph *G = S->G;
+    uint32_t c0 = (uint32_t)u, c1 = (uint32_t)(u >> 32);
+    uint32_t w[4], v[4];
+    philox_block(S->seed, c0, c1, t, 0u, w);
+    philox_block(S->seed, c0, c1, t, 1u, v);
+    uint64_t steps = G->path_off[G->n_paths];
+    uint64_t g = mulhi64((uint64_t)w[0] | ((uint64_t)w[1] << 32), steps);
+    uint32_t p = find_path(G, g);
+    uint64_t off = G->path_off[p];
+    uint64_t n = G->path_off[p + 1] - off;
+    uint64_t i = g - off;
+    memset(r, 0, sizeof *r);
+    r->g = g; r->path = p; r->i = i;
+    r->cooling = (2ull * t >= S->T) || (w[2] & 1u);
+    r->e_i = (w[2] >> 2) & 1u;
+    r->e_j = (w[2] >> 3) & 1u;
+    if (n < 2) { r->skip = 1; r->j = i; return; }
+    uint64_t j;
+    if (r->cooling) {
+        uint64_t k = zipf_draw(&S->zipf[p], v, S->seed, c0, c1, t);
+        int fwd = (w[2] >> 1) & 1u;
+        int can_fwd = i + k < n, can_bwd = i >= k;
+        if (fwd && can_fwd) j = i + k;
+        else if (!fwd && can_bwd) j = i - k;
+        else if (can_fwd) j = i + k;
+        else if (can_bwd) j = i - k;
+        else j = (n - 1 - i > i) ? n - 1 : 0;
+    } else {
+        uint64_t x = mulhi64((uint64_t)v[0] | ((uint64_t)v[1] << 32), n - 1);
+        j = x + (x >= i);
+    }
+    r->j = j;
+    int64_t a = endpoint_pos(G, off + i, r->e_i);
+    int64_t b = endpoint_pos(G, off + j, r->e_j);
+    r->d_ref = a > b ? a - b : b - a;
+    if (r->d_ref == 0) r->skip = 2;
+}
+
+static int sampler_init(sampler_t *S, const orc_graph *G, uint32_t T, double theta, uint64_t seed)
+{
+    S->G = G; S->T = T; S->seed = seed;
+    S->zipf = (zipf_t *)calloc(G->n_paths ? G->n_paths : 1, sizeof(zipf_t));
+    if (!S->zipf) return -1;
+    for (uint32_t p = 0; p < G->n_paths; ++p) {
+        uint64_t n = G->path_off[p + 1] - G->path_off[p];
+        if (n >= 2) S->zipf[p] = zipf_setup(theta, n - 1);
+    }
+    return 0;
+}
+
+static void sampler_free(sampler_t *S) { free(S->zipf); }
+
+#define GRAPH_ARGS const uint32_t *node_len, uint32_t n_nodes, const uint64_t *path_off, \
+    uint32_t n_paths, const uint32_t *step_node, const uint8_t *step_rev, const int64_t *step_pos
+#define GRAPH_INIT orc_graph G = {n_nodes, n_paths, node_len, path_off, step_node, step_rev, step_pos}
+
+int orc_sample(GRAPH_ARGS, uint32_t T, uint32_t t, double theta, uint64_t seed,
+               uint64_t u_begin, uint64_t count, orc_sample_rec *out)
+{
+    GRAPH_INIT;
+    sampler_t S;
+    if (sampler_init(&S, &G, T, theta, seed)) return -1;
+    for (uint64_t q = 0; q < count; ++q) sample_update(&S, t, u_begin + q, &out[q]);
+    sampler_free(&S);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Learning-rate schedule (Algorithm 1, line 3; annealing of Zheng).   */
+/* ------------------------------------------------------------------ */
+
+void orc_eta_schedule(uint32_t T, double eta_max, double eta_min, double *eta)
+{
+    if (T == 1) { eta[0] = eta_max; return; }
+    double lambda = log(eta_max / eta_min) / (double)(T - 1);
+    for (uint32_t t = 0; t < T; ++t) eta[t] = eta_max * exp(-lambda * (double)t);
+}
+
+/* ------------------------------------------------------------------ */
+/* The update (Algorithm 1, lines 14-15) in FP64.                      */
+/* ------------------------------------------------------------------ */
+
+static void update_delta(const double vi[2], const double vj[2], double d_ref, double eta,
+                         double out[4], int *moved)
+{
+    double dx = vi[0] - vj[0], dy = vi[1] - vj[1];
+    double mag = sqrt(dx * dx + dy * dy);
+    *moved = 0;
+    memset(out, 0, 4 * sizeof(double));
+    if (mag == 0.0) return;
+    double w = 1.0 / (d_ref * d_ref);
+    double mu = eta * w;
+    if (mu > 1.0) mu = 1.0;
+    double r = mu * (mag - d_ref) / (2.0 * mag);
+    out[0] = -r * dx; out[1] = -r * dy; /* change of v_i */
+    out[2] = r * dx;  out[3] = r * dy;  /* change of v_j */
+    *moved = 1;
+}
+
+/* Jacobi sweep: the change every update of [u_begin, u_begin + count) of     */
+/* iteration t would make to its two points, all computed from the same      */
+/* frozen layout xy [n_nodes][4] = (sx, sy, ex, ey). Skipped updates give 0. */
+int orc_sweep(GRAPH_ARGS, const double *xy, uint32_t T, uint32_t t, double eta,
+              double theta, uint64_t seed, uint64_t u_begin, uint64_t count, double *delta)
+{
+    GRAPH_INIT;
+    sampler_t S;
+    if (sampler_init(&S, &G, T, theta, seed)) return -1;
+    for (uint64_t q = 0; q < count; ++q) {
+        orc_sample_rec r;
+        sample_update(&S, t, u_begin + q, &r);
+        double *out = delta + 4 * q;
+        memset(out, 0, 4 * sizeof(double));
+        if (r.skip) continue;
+        uint64_t off = G.path_off[r.path];
+        uint32_t ni = G.step_node[off + r.i], nj = G.step_node[off + r.j];
+        double vi[2] = {xy[4 * (uint64_t)ni + 2 * r.e_i], xy[4 * (uint64_t)ni + 2 * r.e_i + 1]};
+        double vj[2] = {xy[4 * (uint64_t)nj + 2 * r.e_j], xy[4 * (uint64_t)nj + 2 * r.e_j + 1]};
+        int moved;
+        update_delta(vi, vj, (double)r.d_ref, eta, out, &moved);
+    }
+    sampler_free(&S);
+    return 0;
+}
+
+/* Hogwild! layout loop. Threads share xy with relaxed atomic loads/stores */
+/* of each coordinate, so a concurrent update may be lost or read stale,    */
+/* as in the paper's CPU and GPU executions. n_threads = 1 is sequential.   */
+typedef struct {
+    const sampler_t *S;
+    double *xy;
+    uint32_t t;
+    double eta;
+    uint64_t u0, u1;
+    uint64_t moved;
+} layout_job;
+
+static double ld_relaxed(double *p)
+{
+    uint64_t bits = __atomic_load_n((uint64_t *)p, __ATOMIC_RELAXED);
+    double d; memcpy(&d, &bits, 8); return d;
+}
+
+static void st_relaxed(double *p, double v)
+{
+    uint64_t bits; memcpy(&bits, &v, 8);
+    __atomic_store_n((uint64_t *)p, bits, __ATOMIC_RELAXED);
+}
+
+static void *layout_worker(void *arg)
+{
+    layout_job *J = (layout_job *)arg;
+    const orc_graph *G = J->S->G;
+    uint64_t moved = 0;
+    for (uint64_t u = J->u0; u < J->u1; ++u) {
+        orc_sample_rec r;
+        sample_update(J->S, J->t, u, &r);
+        if (r.skip) continue;
+        uint64_t off = G->path_off[r.path];
+        uint32_t ni = G->step_node[off + r.i], nj = G->step_node[off + r.j];
+        double *pi = J->xy + 4 * (uint64_t)ni + 2 * r.e_i;
+        double *pj = J->xy + 4 * (uint64_t)nj + 2 * r.e_j;
+        double vi[2] = {ld_relaxed(pi), ld_relaxed(pi + 1)};
+        double vj[2] = {ld_relaxed(pj), ld_relaxed(pj + 1)};
+        double d[4];
+        int mv;
+        update_delta(vi, vj, (double)r.d_ref, J->eta, d, &mv);
+        if (!mv) continue;
+        st_relaxed(pi, vi[0] + d[0]);
+        st_relaxed(pi + 1, vi[1] + d[1]);
+        st_relaxed(pj, vj[0] + d[2]);
+        st_relaxed(pj + 1, vj[1] + d[3]);
+        ++moved;
+    }
+    J->moved = moved;
+    return NULL;
+}
+
+/* Runs iterations [t_begin, t_end) of a T-iteration schedule eta[T] with   */
+/* n_updates updates each (Algorithm 1 uses 10 * S). xy is updated in place.*/
+int orc_layout(GRAPH_ARGS, double *xy, uint32_t T, const double *eta, double theta,
+               uint64_t seed, uint32_t t_begin, uint32_t t_end, uint64_t n_updates,
+               uint32_t n_threads, uint64_t *moved_out)
+{
+    GRAPH_INIT;
+    sampler_t S;
+    if (sampler_init(&S, &G, T, theta, seed)) return -1;
+    if (n_threads < 1) n_threads = 1;
+    layout_job *jobs = (layout_job *)calloc(n_threads, sizeof(layout_job));
+    pthread_t *th = (pthread_t *)calloc(n_threads, sizeof(pthread_t));
+    uint64_t moved = 0;
+    for (uint32_t t = t_begin; t < t_end; ++t) {
+        for (uint32_t k = 0; k < n_threads; ++k) {
+            jobs[k].S = &S; jobs[k].xy = xy; jobs[k].t = t; jobs[k].eta = eta[t];
+            jobs[k].u0 = n_updates * k / n_threads;
+            jobs[k].u1 = n_updates * (k + 1) / n_threads;
+        }
+        if (n_threads == 1) {
+            layout_worker(&jobs[0]);
+        } else {
+            for (uint32_t k = 0; k < n_threads; ++k) pthread_create(&th[k], NULL, layout_worker, &jobs[k]);
+            for (uint32_t k = 0; k < n_threads; ++k) pthread_join(th[k], NULL);
+        }
+        for (uint32_t k = 0; k < n_threads; ++k) moved += jobs[k].moved;
+    }
+    if (moved_out) *moved_out = moved;
+    free(jobs); free(th);
+    sampler_free(&S);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sampled path stress (Eq. 2) with its 95 % confidence interval.      */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    const orc_graph *G;
+    const double *xy;
+    uint64_t seed;
+    uint32_t per_step;
+    double mean;          /* second pass only */
+    uint32_t p0, p1;      /* paths handled by this job */
+    double *per_path;     /* [n_paths][3] sum, sum of squared deviations, n */
+    int pass;
+} stress_job;
+
+/* Stress term of sample q of path p, or -1 when d_ref = 0. */
+static double stress_term(const orc_graph *G, const double *xy, uint64_t seed, uint32_t p,
+                          uint64_t q, int64_t *d_out)
+{
+    uint64_t off = G->path_off[p], n = G->path_off[p + 1] - off;
+    uint32_t c0 = (uint32_t)q, c1 = (uint32_t)(q >> 32), c2 = 0x80000000u | p;
+    uint32_t w[4], v[4];
+    philox_block(seed, c0, c1, c2, 0u, w);
+    philox_block(seed, c0, c1, c2, 1u, v);
+    uint64_t i = mulhi64((uint64_t)w[0] | ((uint64_t)w[1] << 32), n);
+    uint64_t x = mulhi64((uint64_t)v[0] | ((uint64_t)v[1] << 32), n - 1);
+    uint64_t j = x + (x >= i);
+    int ei = w[2] & 1u, ej = (w[2] >> 1) & 1u;
+    int64_t a = endpoint_pos(G, off + i, ei), b = endpoint_pos(G, off + j, ej);
+    int64_t d = a > b ? a - b : b - a;
+    *d_out = d;
+    if (d == 0) return -1.0;
+    uint32_t ni = G->step_node[off + i], nj = G->step_node[off + j];
+    double dx = xy[4 * (uint64_t)ni + 2 * ei] - xy[4 * (uint64_t)nj + 2 * ej];
+    double dy = xy[4 * (uint64_t)ni + 2 * ei + 1] - xy[4 * (uint64_t)nj + 2 * ej + 1];
+    double mag = sqrt(dx * dx + dy * dy);
+    double s = (mag - (double)d) / (double)d;
+    return s * s;
+}
+
+static void *stress_worker(void *arg)
+{
+    stress_job *J = (stress_job *)arg;
+    const orc_graph *G = J->G;
+    for (uint32_t p = J->p0; p < J->p1; ++p) {
+        uint64_t n = G->path_off[p + 1] - G->path_off[p];
+        double acc = 0.0, cnt = 0.0;
+        if (n >= 2) {
+            uint64_t Q = (uint64_t)J->per_step * n;
+            for (uint64_t q = 0; q < Q; ++q) {
+                int64_t d;
+                double term = stress_term(G, J->xy, J->seed, p, q, &d);
+                if (term < 0.0) continue;
+                if (J->pass == 0) acc += term;
+                else acc += (term - J->mean) * (term - J->mean);
+                cnt += 1.0;
+            }
+        }
+        J->per_path[3 * (uint64_t)p + (J->pass == 0 ? 0 : 1)] = acc;
+        if (J->pass == 0) J->per_path[3 * (uint64_t)p + 2] = cnt;
+    }
+    return NULL;
+}
+
+/* out = {mean, stddev, ci95_lo, ci95_hi, n_valid, n_skipped_dref0}.        */
+/* per_path (optional, [n_paths][3]): sum of terms, sum of squared          */
+/* deviations from the global mean, number of valid samples.                */
+int orc_sampled_stress(GRAPH_ARGS, const double *xy, uint32_t per_step, uint64_t seed,
+                       uint32_t n_threads, double *out, double *per_path)
+{
+    GRAPH_INIT;
+    if (n_threads < 1) n_threads = 1;
+    double *pp = per_path ? per_path : (double *)calloc(3 * (size_t)(n_paths ? n_paths : 1), sizeof(double));
+    if (!pp) return -1;
+    memset(pp, 0, 3 * (size_t)n_paths * sizeof(double));
+    stress_job *jobs = (stress_job *)calloc(n_threads, sizeof(stress_job));
+    pthread_t *th = (pthread_t *)calloc(n_threads, sizeof(pthread_t));
+    double total = 0.0, n_valid = 0.0, n_all = 0.0, mean = 0.0, ss = 0.0;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (uint32_t k = 0; k < n_threads; ++k) {
+            stress_job *J = &jobs[k];
+            J->G = &G; J->xy = xy; J->seed = seed; J->per_step = per_step; J->mean = mean;
+            J->per_path = pp; J->pass = pass;
+            J->p0 = (uint32_t)((uint64_t)n_paths * k / n_threads);
+            J->p1 = (uint32_t)((uint64_t)n_paths * (k + 1) / n_threads);
+        }
+        if (n_threads == 1) stress_worker(&jobs[0]);
+        else {
+            for (uint32_t k = 0; k < n_threads; ++k) pthread_create(&th[k], NULL, stress_worker, &jobs[k]);
+            for (uint32_t k = 0; k < n_threads; ++k) pthread_join(th[k], NULL);
+        }
+        if (pass == 0) {
+            for (uint32_t p = 0; p < n_paths; ++p) {
+                uint64_t n = path_off[p + 1] - path_off[p];
+                total += pp[3 * (uint64_t)p];
+                n_valid += pp[3 * (uint64_t)p + 2];
+                if (n >= 2) n_all += (double)per_step * (double)n;
+            }
+            mean = n_valid > 0 ? total / n_valid : 0.0;
+        } else {
+            for (uint32_t p = 0; p < n_paths; ++p) ss += pp[3 * (uint64_t)p + 1];
+        }
+    }
+    double sd = n_valid > 1 ? sqrt(ss / (n_valid - 1.0)) : 0.0;
+    double half = n_valid > 0 ? 1.96 * sd / sqrt(n_valid) : 0.0;
+    out[0] = mean; out[1] = sd; out[2] = mean - half; out[3] = mean + half;
+    out[4] = n_valid; out[5] = n_all - n_valid;
+    free(jobs); free(th);
+    if (!per_path) free(pp);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Path stress (Eq. 1): every unordered pair of distinct steps of a path,  */
+/* the mean over its endpoint combinations with d_ref > 0; the pairs with   */
+/* none are left out of the count. Quadratic: small graphs only.           */
+/* ------------------------------------------------------------------ */
+
+int orc_full_stress(GRAPH_ARGS, const double *xy, double *out)
+{
+    GRAPH_INIT;
+    double total = 0.0, pairs = 0.0;
+    for (uint32_t p = 0; p < n_paths; ++p) {
+        uint64_t off = path_off[p], n = path_off[p + 1] - off;
+        for (uint64_t i = 0; i < n; ++i) {
+            for (uint64_t j = i + 1; j < n; ++j) {
+                double sum = 0.0;
+                int valid = 0;
+                for (int ei = 0; ei < 2; ++ei) {
+                    for (int ej = 0; ej < 2; ++ej) {
+                        int64_t a = endpoint_pos(&G, off + i, ei), b = endpoint_pos(&G, off + j, ej);
+                        int64_t d = a > b ? a - b : b - a;
+                        if (d == 0) continue;
+                        uint32_t ni = step_node[off + i], nj = step_node[off + j];
+                        double dx = xy[4 * (uint64_t)ni + 2 * ei] - xy[4 * (uint64_t)nj + 2 * ej];
+                        double dy = xy[4 * (uint64_t)ni + 2 * ei + 1] - xy[4 * (uint64_t)nj + 2 * ej + 1];
+                        double mag = sqrt(dx * dx + dy * dy);
+                        double s = (mag - (double)d) / (double)d;
+                        sum += s * s;
+                        ++valid;
+                    }
+                }
+                if (valid) { total += sum / valid; pairs += 1.0; }
+            }
+        }
+    }
+    out[0] = pairs > 0 ? total / pairs : 0.0;
+    out[1] = pairs;
+    return 0;
+}

@@ -1,0 +1,111 @@
+"""Pins for the oracle's path stress (Eq. 1) and sampled path stress (Eq. 2)."""
+import json
+import os
+from fractions import Fraction
+
+import numpy as np
+
+import oracle as O
+from synth import make_custom, make_graph
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _three_node():
+    with open(os.path.join(GOLDEN, "path_stress_3node.json")) as f:
+        gold = json.load(f)
+    g = make_custom([2, 3, 1], [[(0, 0), (1, 0), (2, 0)]],
+                    init_xy=np.array(gold["layout"], dtype=np.float64))
+    return g, gold
+
+
+def test_path_stress_hand_worked_example():
+    g, gold = _three_node()
+    val, pairs = O.full_stress(g, g.init_xy)
+    assert pairs == 3
+    want = float(Fraction(*gold["path_stress"]))
+    assert abs(val - want) <= 1e-15
+
+
+def test_sampled_stress_converges_to_its_exact_expectation():
+    g, gold = _three_node()
+    r = O.sampled_stress(g, g.init_xy, per_step=200_000, seed=5)
+    want = float(Fraction(*gold["expected_sampled_term"]))
+    assert abs(r["mean"] - want) < 4 * r["std"] / np.sqrt(r["n_valid"])
+    # 2 of the 12 ordered endpoint choices have d_ref = 0 and are left out of n
+    n_all = 200_000 * 3
+    assert abs(r["n_skipped"] / n_all - 2 / 12) < 5 * np.sqrt((1 / 6) * (5 / 6) / n_all)
+    assert r["n_valid"] + r["n_skipped"] == n_all
+
+
+def test_confidence_interval_formula_and_second_pass_sigma():
+    g = make_graph("tiny")
+    r = O.sampled_stress(g, g.init_xy, per_step=20, seed=3)
+    half = 1.96 * r["std"] / np.sqrt(r["n_valid"])
+    assert abs(r["ci_lo"] - (r["mean"] - half)) < 1e-15 * (1 + abs(r["mean"]))
+    assert abs(r["ci_hi"] - (r["mean"] + half)) < 1e-15 * (1 + abs(r["mean"]))
+
+
+def test_single_path_sampled_stress_is_unbiased_for_all_pair_average():
+    # one path: every (i, j != i, e_i, e_j) equally likely, so the sampled mean
+    # estimates the average term over all valid ordered choices (brute force)
+    rng = np.random.default_rng(0)
+    n = 40
+    lens = rng.integers(1, 9, size=n).astype(np.uint32)
+    xy = np.cumsum(np.r_[0, lens[:-1]]).astype(np.float64)
+    xy = np.stack([xy, np.zeros(n), xy + lens, np.zeros(n)], 1) + rng.normal(0, 2.0, (n, 4))
+    g = make_custom(lens, [[(v, int(rng.integers(0, 2))) for v in range(n)]], init_xy=xy)
+    pos = g.step_pos
+    rev = g.step_rev
+    terms = []
+    for i in range(n):
+        for j in range(n):
+            if i == j:
+                continue
+            for ei in range(2):
+                for ej in range(2):
+                    a = pos[i] + (lens[i] if (ei ^ rev[i]) else 0)
+                    b = pos[j] + (lens[j] if (ej ^ rev[j]) else 0)
+                    d = abs(int(a) - int(b))
+                    if d == 0:
+                        continue
+                    dx = xy[i, 2 * ei] - xy[j, 2 * ej]
+                    dy = xy[i, 2 * ei + 1] - xy[j, 2 * ej + 1]
+                    terms.append(((np.hypot(dx, dy) - d) / d) ** 2)
+    want = np.mean(terms)
+    r = O.sampled_stress(g, xy, per_step=20_000, seed=8)
+    assert abs(r["mean"] - want) < 4 * r["std"] / np.sqrt(r["n_valid"])
+
+
+def test_sampled_stress_tracks_full_stress_across_layouts():
+    # Section V-B, Fig. 11: sampled path stress follows path stress over
+    # layouts of different quality (r = 0.995 in the paper)
+    g = make_graph("tiny", backbone=300, paths=4)
+    rng = np.random.default_rng(1)
+    base = g.init_xy + rng.normal(0, 50, g.init_xy.shape)
+    full, samp = [], []
+    for it in [0, 1, 2, 3, 5, 8, 12, 16, 20, 25, 30]:
+        xy = O.layout(g, base, T=30, seed=it, t_end=it)[0] if it else base
+        full.append(O.full_stress(g, xy)[0])
+        samp.append(O.sampled_stress(g, xy, seed=it)["mean"])
+    r = np.corrcoef(np.log(full), np.log(samp))[0, 1]
+    assert r > 0.97
+
+
+def test_sampled_stress_stable_across_sampling_seeds():
+    g = make_graph("tiny")
+    xy, _ = O.layout(g, g.init_xy, seed=1)
+    vals = [O.sampled_stress(g, xy, seed=s) for s in range(5)]
+    m = np.array([v["mean"] for v in vals])
+    for v in vals:
+        # every estimate sits inside the others' confidence intervals' span
+        assert v["ci_lo"] <= m.mean() <= v["ci_hi"] or abs(v["mean"] - m.mean()) < 4 * (v["ci_hi"] - v["ci_lo"])
+
+
+def test_threaded_stress_matches_sequential():
+    g = make_graph("tiny")
+    a = O.sampled_stress(g, g.init_xy, seed=2, n_threads=1, per_path=True)
+    b = O.sampled_stress(g, g.init_xy, seed=2, n_threads=3, per_path=True)
+    assert a["n_valid"] == b["n_valid"]
+    np.testing.assert_array_equal(a["per_path"][:, 0], b["per_path"][:, 0])
+    assert abs(a["mean"] - b["mean"]) <= 1e-14 * a["mean"]
