@@ -1,0 +1,389 @@
+"""Benchmark: PG-SGD layout updates/s on the 5 M-node synthetic chromosome graph.
+
+One step = one whole layout of the graph (Algorithm 1: 30 iterations of
+10 x S lock-free updates, S = total path steps) followed by its sampled path
+stress (Eq. 2, 100 samples per step), starting every step from the same
+initial layout. Inputs are resident in HBM when the timed region starts
+(3.9 GB of packed records: larger than L2, so no flush is needed).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--config chrom|mid|tiny]
+    python bench.py --impl reference ...   # the CPU oracle on the host cores
+
+Multi-GPU: the layout does not shard (every path crosses the shared backbone),
+so N > 1 runs N independent replicas, one per GPU, under torchrun; the line
+reports their aggregate throughput ("weak" scaling, no collective on the data
+path: the process group only times the replicas).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PG-SGD updates/sec and % HBM roofline on 5M-node graph; stress vs oracle"
+UNIT = "updates/s"
+ITERS = 30
+THETA = 0.99
+SEED = 1
+STRESS_PER_STEP = 100
+STRESS_SEED = 7
+# DRAM sectors an update touches with no cache reuse: 2 step-record sectors and
+# 2 node-record sectors read, 2 node-record sectors written back (32 B each).
+BYTES_PER_UPDATE = 192
+WORKLOADS = {
+    "chrom": "synthetic chromosome-scale pangenome: 5,000,000 backbone nodes (+10% bubble "
+             "nodes), 90 paths, ~4.7e8 steps, node length geometric mean 30 bp with a 1e-4 "
+             "tail to 100 kb; 30 iterations x 10 x steps updates; theta 0.99",
+    "mid": "synthetic pangenome: 200,000 backbone nodes, 32 paths, ~7e6 steps",
+    "tiny": "synthetic pangenome: 2,000 backbone nodes, 8 paths, ~1.6e4 steps",
+}
+
+
+# ---------------------------------------------------------------- distributed
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(backend):
+    import torch.distributed as dist
+    ws, rank, _ = dist_env()
+    if ws > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend, rank=rank, world_size=ws)
+    return ws, rank
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    """Largest value of x over all ranks (x itself without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={','.join(self.FIELDS)}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        top = max(sm)
+        loaded = [s for s in sm if s >= 0.5 * top] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- workload
+
+def make_workload(config):
+    from synth import make_graph
+    return make_graph(config)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def cpu_baseline(g, budget_s=12.0, warmup=False):
+    """The oracle (threaded Hogwild! mode, all host cores) on the first updates
+    of iteration 0 of the same workload, sized to take about budget_s."""
+    import oracle as O
+    threads = os.cpu_count() or 1
+    eta = O.eta_schedule(ITERS, O.default_eta_max(g))
+    probe = max(100_000, min(g.n_steps, 2_000_000))
+    t0 = time.perf_counter()
+    O.layout(g, g.init_xy, T=ITERS, eta=eta, theta=THETA, seed=SEED, t_end=1, n_updates=probe,
+             n_threads=threads)
+    rate = probe / max(time.perf_counter() - t0, 1e-6)
+    n = int(min(max(rate * budget_s, probe), 10 * g.n_steps))
+    t0 = time.perf_counter()
+    O.layout(g, g.init_xy, T=ITERS, eta=eta, theta=THETA, seed=SEED, t_end=1, n_updates=n,
+             n_threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {n} updates of iteration 0 of the same graph and seed "
+                      f"({n / (10 * g.n_steps):.3%} of one iteration), FP64, {threads} threads, "
+                      f"{dt:.1f} s"}
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if ws > 1 and rank != 0:
+        return 0
+    g = make_workload(args.config)
+    import oracle as O
+    O.build()
+    for _ in range(args.warmup):
+        cpu_baseline(g, budget_s=args.ref_budget)
+    vals = [cpu_baseline(g, budget_s=args.ref_budget) for _ in range(args.steps)]
+    value = statistics.mean(v["value"] for v in vals)
+    cb = dict(vals[-1])
+    cb["value"] = value
+    updates_per_step = ITERS * 10 * g.n_steps
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": updates_per_step / value * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.config], "name": args.config,
+                   "sample": "each step times a bounded sample of the layout (see cpu_baseline)"},
+        "cpu_baseline": cb,
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    init_dist("nccl" if ws > 1 else "gloo")
+    dev = torch.device("cuda", local)
+    import paper_2409_00876_gb300 as pg
+    pg.load_library()
+
+    g = make_workload(args.config)
+    xy0 = torch.from_numpy(g.init_xy).to(dev)
+    G = pg.Graph.from_synth(g)
+    G.set_coords(xy0)
+    info = G.info()
+    S = info["n_steps"]
+    updates_per_step = ITERS * 10 * S
+    stream = torch.cuda.current_stream()
+
+    def step(timing=False):
+        G.set_coords(xy0)
+        G.layout(ITERS, theta=THETA, seed=SEED)
+        return G.stress(STRESS_PER_STEP, seed=STRESS_SEED)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    G.set_option("timing", 1)
+    G.timing_read(reset=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st = None
+    for _ in range(args.steps):
+        st = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    upd_ms, launches, upd = G.timing_read(reset=True)
+    G.set_option("timing", 0)
+    ms_max = max_over_ranks(ms, dev)
+    total_updates = sum_over_ranks(updates_per_step * args.steps, dev)
+    value = total_updates / (ms_max / 1e3)
+
+    # kernels launched per step: set_coords, 30 x (update + rebase), stress + finalize
+    gpu_launches = args.steps * (1 + 2 * ITERS + 2)
+    peak, peak_kind = peaks()
+    per_launch_ms = upd_ms / max(launches, 1)
+    updates_per_launch = upd / max(launches, 1)
+    achieved = BYTES_PER_UPDATE * updates_per_launch / (per_launch_ms / 1e3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "update_kernel_traffic.json")
+    if os.path.exists(tpath):
+        tr = json.load(open(tpath))
+        if tr.get("config") == args.config and tr.get("kernel_rev") == kernel_revision():
+            traffic = tr["bytes_per_update"] * updates_per_launch
+
+    # end to end through the public API with host buffers, copies inside the region
+    e2e = run_e2e(pg, g, args, dev) if not args.skip_e2e else None
+    if e2e is not None:
+        e2e["value"] = sum_over_ranks(e2e.pop("updates"), dev) / max_over_ranks(e2e.pop("seconds"), dev)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.skip_cpu:
+        cpu = cpu_baseline(g, budget_s=args.cpu_budget)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.config], "name": args.config,
+                       "n_nodes": info["n_nodes"], "n_paths": info["n_paths"], "n_steps": S,
+                       "iterations": ITERS, "updates_per_step": updates_per_step,
+                       "stress_samples_per_step": STRESS_PER_STEP * S,
+                       "l2": f"inputs larger than L2 ({info['device_bytes'] / 1e9:.1f} GB resident), no flush",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "stress": {"mean": st["mean"], "ci_lo": st["ci_lo"], "ci_hi": st["ci_hi"],
+                       "n_valid": st["n_valid"]},
+            "layout_only_updates_per_s": upd / (upd_ms / 1e3) if upd_ms > 0 else None,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "update_kernel", "bytes_per_update_model": BYTES_PER_UPDATE,
+                         "peak_kind": peak_kind, "launch_ms": per_launch_ms},
+            "clocks": clk,
+            "gpu_launches": gpu_launches,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_e2e(pg, g, args, dev):
+    import torch
+    # pinned host inputs: the graph arrays and the initial layout
+    host = {k: torch.from_numpy(np.ascontiguousarray(getattr(g, k))).pin_memory()
+            for k in ("node_len", "path_off", "step_node", "step_rev", "step_pos")}
+    xy_in = torch.from_numpy(g.init_xy).pin_memory()
+    xy_out = torch.empty_like(xy_in).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in host.values()) + xy_in.numel() * 8
+    d2h = xy_out.numel() * 8 + 48
+
+    def one():
+        G = pg.Graph(host["node_len"].numpy(), host["path_off"].numpy(), host["step_node"].numpy(),
+                     host["step_rev"].numpy(), host["step_pos"].numpy())
+        G.set_coords(xy_in.numpy())
+        G.layout(ITERS, theta=THETA, seed=SEED)
+        G.stress(STRESS_PER_STEP, seed=STRESS_SEED)
+        G.get_coords(xy_out.numpy())
+        G.close()
+
+    one()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    k = max(1, args.e2e_steps)
+    for _ in range(k):
+        one()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"unit": UNIT, "updates": ITERS * 10 * g.n_steps * k, "seconds": dt, "steps": k,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+
+def kernel_revision():
+    """Hash of the update kernel's sources: ncu traffic counts are only valid for it."""
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("pgsgd_kernels.cu", "pgsgd_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2409_00876_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--config", default="chrom", choices=list(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--ref-budget", type=float, default=10.0)
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "gb300" and not os.environ.get("PGSGD_BENCH_ALLOW_SHORT"):
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

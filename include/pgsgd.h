@@ -1,0 +1,230 @@
+/*
+ * pgsgd.h - C ABI of libpgsgd.so: path-guided SGD (PG-SGD) layout of a
+ * pangenome variation graph on one NVIDIA GB300 GPU (sm_103a), and the
+ * sampled path-stress metric that scores it.
+ *
+ * The method is the one of "Rapid GPU-Based Pangenome Graph Layout" (SC24):
+ * Algorithm 1 (Section II-C) moves the two endpoints of randomly chosen
+ * same-path node pairs towards their path distance, millions of times per
+ * iteration, without locks (Hogwild!, Section III-A); Eq. 2 (Section V-B)
+ * scores a layout by sampling such pairs.
+ *
+ * Conventions for every entry point:
+ *   - The return value is a status code (pgsgd_status). On failure the
+ *     calling thread's message is available from pgsgd_last_error().
+ *   - `cuda_stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *     default stream). Work is queued on it in order.
+ *   - `on_device` = 1 means a pointer is CUDA device memory (for example a
+ *     torch tensor's data_ptr()); 0 means host memory. Data is always copied:
+ *     the library never keeps a caller's pointer after the call returns.
+ *   - A graph handle must not be used from two host threads at once.
+ *   - All memory the library allocates is owned by the handle and released
+ *     by pgsgd_destroy().
+ */
+#ifndef PGSGD_H
+#define PGSGD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pgsgd_status {
+    PGSGD_OK = 0,
+    PGSGD_EINVAL = 1,   /* bad argument or inconsistent input array */
+    PGSGD_ERANGE = 2,   /* a value overflows the packed device records */
+    PGSGD_ENOMEM = 3,   /* host or device allocation failed */
+    PGSGD_ECUDA = 4,    /* a CUDA call or kernel failed */
+    PGSGD_ETIMEOUT = 5, /* a device-side bounded wait expired */
+    PGSGD_EDEVICE = 6   /* a device-side bounds check tripped */
+} pgsgd_status;
+
+/* Options for pgsgd_set_option / pgsgd_get_option. */
+typedef enum pgsgd_option {
+    /* Coordinate storage. 0 = anchored (default): each node keeps an integer
+     * anchor per axis and FP32 offsets from it, so FP32 keeps sub-nucleotide
+     * resolution at chromosome scale (coordinates up to about 1e9).
+     * 1 = plain FP32 absolute coordinates. Takes effect at pgsgd_set_coords. */
+    PGSGD_OPT_COORD_MODE = 1,
+    /* Updates per iteration = this value times the number of path steps
+     * (Algorithm 1, line 1 uses 10). Default 10. */
+    PGSGD_OPT_UPDATES_PER_STEP = 2,
+    /* Update-kernel launch shape: threads per block (64..1024, multiple of
+     * 32; default 256), resident blocks per SM in the grid (default 8), and
+     * updates each thread keeps in flight per loop trip (1, 2 or 4; default 2). */
+    PGSGD_OPT_BLOCK = 3,
+    PGSGD_OPT_BLOCKS_PER_SM = 4,
+    PGSGD_OPT_UPDATES_PER_THREAD = 5,
+    /* 0 = plain stores of the moved points (last writer wins, as in the
+     * paper's kernels; default), 1 = vector atomic adds of the moves. */
+    PGSGD_OPT_ATOMIC_UPDATES = 6,
+    /* 1 = after each iteration, move every anchor to the rounded current
+     * start point so the FP32 offsets stay small (anchored mode; default 1). */
+    PGSGD_OPT_REBASE = 7,
+    /* 1 = record CUDA events around every update-kernel launch on the
+     * launching stream; read them with pgsgd_timing_read. Default 0. */
+    PGSGD_OPT_TIMING = 8,
+    /* Concurrency cap: the update kernel's grid is shrunk so that at most this
+     * many updates are in flight at once (0 = no cap). Small graphs under a
+     * full GB300 grid would otherwise see many simultaneous updates per node. */
+    PGSGD_OPT_MAX_CONCURRENT = 9
+} pgsgd_option;
+
+/* Device-resident graph: node records, packed step records, path table. */
+typedef struct pgsgd_graph pgsgd_graph;
+
+/* Result of pgsgd_stress (Eq. 2 and the interval of Section V-B). */
+typedef struct pgsgd_stress_result {
+    double mean;        /* sampled path stress: sum of terms / n_valid */
+    double stddev;      /* sample standard deviation of the terms */
+    double ci_lo;       /* mean - 1.96 stddev / sqrt(n_valid) */
+    double ci_hi;       /* mean + 1.96 stddev / sqrt(n_valid) */
+    uint64_t n_valid;   /* samples with d_ref > 0 */
+    uint64_t n_skipped; /* samples with d_ref = 0 (no defined term) */
+} pgsgd_stress_result;
+
+/* One drawn update, as pgsgd_debug_sample reports it (40 bytes). */
+typedef struct pgsgd_sample {
+    uint64_t g;       /* global step index drawn, in [0, S) */
+    uint64_t i;       /* step index of n_i within its path */
+    uint64_t j;       /* step index of n_j within its path */
+    int64_t d_ref;    /* path distance of the two chosen endpoints (nt) */
+    uint32_t path;    /* path id */
+    uint8_t cooling;  /* 1 = power-law pair, 0 = uniform pair */
+    uint8_t e_i;      /* 0 = start point, 1 = end point of n_i */
+    uint8_t e_j;      /* 0 = start point, 1 = end point of n_j */
+    uint8_t skip;     /* 0 = valid, 1 = path has < 2 steps, 2 = d_ref = 0 */
+} pgsgd_sample;
+
+/* Graph summary for callers and benchmarks. */
+typedef struct pgsgd_info {
+    uint64_t n_steps;          /* S = total path steps */
+    uint64_t device_bytes;     /* device memory held by the handle */
+    uint64_t max_path_steps;   /* longest path in steps */
+    int64_t max_path_nt;       /* longest path in nucleotides */
+    uint32_t n_nodes;
+    uint32_t n_paths;
+    int32_t device;            /* CUDA device ordinal the graph lives on */
+    int32_t sm_count;
+} pgsgd_info;
+
+/*
+ * Build the device-resident graph (Section II-A: nodes with sequence lengths
+ * and paths that walk them; Section IV-B1: only the fields the layout reads).
+ *
+ *   node_len[n_nodes]        sequence length of every node, >= 1
+ *   path_off[n_paths + 1]    path p owns steps [path_off[p], path_off[p+1]);
+ *                            path_off[0] = 0, non-decreasing (empty paths ok)
+ *   step_node[S]             node id of every step, < n_nodes
+ *   step_rev[S]              1 = the path traverses the node in reverse, else 0
+ *   step_pos[S]              int64 nucleotide position where the step starts:
+ *                            0 at a path's first step, then the previous
+ *                            step's position plus its node's length
+ * S = path_off[n_paths]. All five arrays are on the host (on_device = 0) or
+ * all on the device (on_device = 1); they are copied and validated on the GPU.
+ * Limits (PGSGD_ERANGE beyond them): n_nodes < 2^31, every step position
+ * < 2^32, n_paths <= 16384. Inconsistent arrays give PGSGD_EINVAL.
+ * Synchronous: returns after the graph is resident. *out receives the handle
+ * (NULL on failure). The graph lives on the current CUDA device.
+ */
+int pgsgd_create(const uint32_t *node_len, uint32_t n_nodes,
+                 const uint64_t *path_off, uint32_t n_paths,
+                 const uint32_t *step_node, const uint8_t *step_rev,
+                 const int64_t *step_pos, int on_device, void *cuda_stream,
+                 pgsgd_graph **out);
+
+/* Release every resource of the handle (NULL is accepted). */
+int pgsgd_destroy(pgsgd_graph *g);
+
+int pgsgd_set_option(pgsgd_graph *g, int option, int64_t value);
+int pgsgd_get_option(const pgsgd_graph *g, int option, int64_t *value);
+int pgsgd_info_get(const pgsgd_graph *g, pgsgd_info *out);
+
+/*
+ * Replace the layout (Algorithm 1, output L: one 2-D segment per node).
+ * xy[n_nodes][4] float64 = (start x, start y, end x, end y), host or device.
+ * Stored in FP32 (anchored mode: integer anchor + FP32 offset per axis,
+ * which needs |coordinate| < 2^30; PGSGD_ERANGE otherwise). Queued on the
+ * stream; the caller's buffer may be reused when the call returns.
+ */
+int pgsgd_set_coords(pgsgd_graph *g, const double *xy, int on_device, void *cuda_stream);
+
+/* Read the layout back into xy[n_nodes][4] float64 (exact value of the
+ * stored FP32 representation). Synchronous for host xy, queued for device xy. */
+int pgsgd_get_coords(pgsgd_graph *g, double *xy, int on_device, void *cuda_stream);
+
+/*
+ * Run iterations [iter_begin, iter_end) of a T = iter_max iteration layout
+ * (Algorithm 1): each iteration launches one update kernel of
+ * N = updates_per_step * S lock-free updates at learning rate eta_t.
+ *   eta      host array of iter_max rates, or NULL for the annealing of
+ *            Zheng et al.: eta_t = eta_max * exp(-lambda t),
+ *            lambda = ln(eta_max / eta_min) / (T - 1)
+ *   eta_max  <= 0 selects (longest path in nucleotides)^2
+ *   eta_min  <= 0 selects 0.01
+ *   theta    Zipf exponent of the power-law pair choice, in [0, 4]
+ *   seed     Philox key; update u of iteration t draws counter (u, t, block)
+ * Iterations t with 2 t >= T always take the power-law pair (cooling).
+ * Running [0, k) then [k, T) gives the same draws as [0, T) (resume).
+ * Requires a layout (pgsgd_set_coords). Asynchronous on the stream.
+ */
+int pgsgd_layout(pgsgd_graph *g, uint32_t iter_max, const double *eta,
+                 double eta_max, double eta_min, double theta, uint64_t seed,
+                 uint32_t iter_begin, uint32_t iter_end, void *cuda_stream);
+
+/*
+ * Sampled path stress of the current layout (Eq. 2, Section V-B): for every
+ * path p with at least two steps, samples_per_step * |p| pairs (the paper
+ * uses 100): step i uniform, step j uniform among the others, a coin for
+ * each endpoint; the term ((|v_i - v_j| - d_ref) / d_ref)^2 in FP32, summed
+ * in FP64; samples with d_ref = 0 are left out of n. Pass seed selects the
+ * sample set (Philox counter (q, 0x80000000 | p, block)).
+ * per_path (optional, host, [n_paths][3] float64): sum of terms, sum of
+ * squared terms, number of valid samples, per path.
+ * Synchronous. Uses a per-handle device scratch buffer.
+ */
+int pgsgd_stress(pgsgd_graph *g, uint32_t samples_per_step, uint64_t seed,
+                 pgsgd_stress_result *out, double *per_path, void *cuda_stream);
+
+/*
+ * The pair each update u in [u_begin, u_begin + count) of iteration t (of
+ * iter_max) draws, written to out[count] (host). Same sampler as the update
+ * kernel; no coordinate is read or written. Synchronous.
+ */
+int pgsgd_debug_sample(pgsgd_graph *g, uint32_t t, uint32_t iter_max, double theta,
+                       uint64_t seed, uint64_t u_begin, uint64_t count,
+                       pgsgd_sample *out, void *cuda_stream);
+
+/*
+ * Jacobi sweep: for every update u in [u_begin, u_begin + count) of
+ * iteration t, the FP32 change it would make to its two points, computed
+ * from the current (frozen) layout at learning rate eta. out[count][4] float32
+ * (host) = (dx_i, dy_i, dx_j, dy_j); skipped updates give zeros. The layout
+ * is not modified. Synchronous.
+ */
+int pgsgd_debug_sweep(pgsgd_graph *g, uint32_t t, uint32_t iter_max, double eta,
+                      double theta, uint64_t seed, uint64_t u_begin, uint64_t count,
+                      float *out, void *cuda_stream);
+
+/*
+ * Update-kernel timing (PGSGD_OPT_TIMING = 1): total milliseconds of all
+ * update-kernel launches since the last reset, measured with CUDA events on
+ * the launching stream, the number of launches and the updates they ran.
+ * Synchronises the recorded events. reset = 1 clears the counters after
+ * reading.
+ */
+int pgsgd_timing_read(pgsgd_graph *g, double *total_ms, uint64_t *launches,
+                      uint64_t *updates, int reset);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char *pgsgd_last_error(void);
+
+/* Constant name of a status code. */
+const char *pgsgd_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PGSGD_H */

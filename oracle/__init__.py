@@ -75,6 +75,8 @@ def _L():
             lib.orc_layout.restype = i32
             lib.orc_sampled_stress.argtypes = gargs + [P, u32, u64, u32, P, P]
             lib.orc_sampled_stress.restype = i32
+            lib.orc_sampled_stress_paths.argtypes = gargs + [P, u32, u64, u32, u32, u32, P, P]
+            lib.orc_sampled_stress_paths.restype = i32
             lib.orc_full_stress.argtypes = gargs + [P, P]
             lib.orc_full_stress.restype = i32
             _lib = lib
@@ -197,13 +199,16 @@ def layout(g, xy, T=30, eta=None, theta=0.99, seed=1, t_begin=0, t_end=None,
     return xy, int(moved[0])
 
 
-def sampled_stress(g, xy, per_step=100, seed=7, n_threads=1, per_path=False):
-    """Eq. 2: dict(mean, std, ci_lo, ci_hi, n_valid, n_skipped[, per_path])."""
+def sampled_stress(g, xy, per_step=100, seed=7, n_threads=1, per_path=False, paths=None):
+    """Eq. 2: dict(mean, std, ci_lo, ci_hi, n_valid, n_skipped[, per_path]).
+
+    paths=(begin, end) restricts the sample set to those paths."""
     xy = np.ascontiguousarray(xy, dtype=np.float64)
     out = np.zeros(6, dtype=np.float64)
     pp = np.zeros((g.n_paths, 3), dtype=np.float64)
-    rc = _L().orc_sampled_stress(*_ga(g).args(), _ptr(xy), int(per_step), int(seed),
-                                 int(n_threads), _ptr(out), _ptr(pp))
+    p0, p1 = (0, g.n_paths) if paths is None else paths
+    rc = _L().orc_sampled_stress_paths(*_ga(g).args(), _ptr(xy), int(per_step), int(seed),
+                                       int(n_threads), int(p0), int(p1), _ptr(out), _ptr(pp))
     if rc:
         raise MemoryError("oracle stress")
     res = dict(mean=out[0], std=out[1], ci_lo=out[2], ci_hi=out[3],

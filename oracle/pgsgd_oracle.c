@@ -635,8 +635,22 @@ static void *stress_worker(void *arg)
 /* out = {mean, stddev, ci95_lo, ci95_hi, n_valid, n_skipped_dref0}.        */
 /* per_path (optional, [n_paths][3]): sum of terms, sum of squared          */
 /* deviations from the global mean, number of valid samples.                */
+/* Paths [p_begin, p_end) only; orc_sampled_stress takes all of them.      */
+int orc_sampled_stress_paths(GRAPH_ARGS, const double *xy, uint32_t per_step, uint64_t seed,
+                             uint32_t n_threads, uint32_t p_begin, uint32_t p_end,
+                             double *out, double *per_path);
+
 int orc_sampled_stress(GRAPH_ARGS, const double *xy, uint32_t per_step, uint64_t seed,
                        uint32_t n_threads, double *out, double *per_path)
+{
+    return orc_sampled_stress_paths(node_len, n_nodes, path_off, n_paths, step_node, step_rev,
+                                    step_pos, xy, per_step, seed, n_threads, 0, n_paths, out,
+                                    per_path);
+}
+
+int orc_sampled_stress_paths(GRAPH_ARGS, const double *xy, uint32_t per_step, uint64_t seed,
+                             uint32_t n_threads, uint32_t p_begin, uint32_t p_end,
+                             double *out, double *per_path)
 {
     GRAPH_INIT;
     if (n_threads < 1) n_threads = 1;
@@ -646,13 +660,15 @@ int orc_sampled_stress(GRAPH_ARGS, const double *xy, uint32_t per_step, uint64_t
     stress_job *jobs = (stress_job *)calloc(n_threads, sizeof(stress_job));
     pthread_t *th = (pthread_t *)calloc(n_threads, sizeof(pthread_t));
     double total = 0.0, n_valid = 0.0, n_all = 0.0, mean = 0.0, ss = 0.0;
+    if (p_end > n_paths) p_end = n_paths;
+    if (p_begin > p_end) p_begin = p_end;
     for (int pass = 0; pass < 2; ++pass) {
         for (uint32_t k = 0; k < n_threads; ++k) {
             stress_job *J = &jobs[k];
             J->G = &G; J->xy = xy; J->seed = seed; J->per_step = per_step; J->mean = mean;
             J->per_path = pp; J->pass = pass;
-            J->p0 = (uint32_t)((uint64_t)n_paths * k / n_threads);
-            J->p1 = (uint32_t)((uint64_t)n_paths * (k + 1) / n_threads);
+            J->p0 = p_begin + (uint32_t)((uint64_t)(p_end - p_begin) * k / n_threads);
+            J->p1 = p_begin + (uint32_t)((uint64_t)(p_end - p_begin) * (k + 1) / n_threads);
         }
         if (n_threads == 1) stress_worker(&jobs[0]);
         else {
@@ -660,7 +676,7 @@ int orc_sampled_stress(GRAPH_ARGS, const double *xy, uint32_t per_step, uint64_t
             for (uint32_t k = 0; k < n_threads; ++k) pthread_join(th[k], NULL);
         }
         if (pass == 0) {
-            for (uint32_t p = 0; p < n_paths; ++p) {
+            for (uint32_t p = p_begin; p < p_end; ++p) {
                 uint64_t n = path_off[p + 1] - path_off[p];
                 total += pp[3 * (uint64_t)p];
                 n_valid += pp[3 * (uint64_t)p + 2];
@@ -668,7 +684,7 @@ int orc_sampled_stress(GRAPH_ARGS, const double *xy, uint32_t per_step, uint64_t
             }
             mean = n_valid > 0 ? total / n_valid : 0.0;
         } else {
-            for (uint32_t p = 0; p < n_paths; ++p) ss += pp[3 * (uint64_t)p + 1];
+            for (uint32_t p = p_begin; p < p_end; ++p) ss += pp[3 * (uint64_t)p + 1];
         }
     }
     double sd = n_valid > 1 ? sqrt(ss / (n_valid - 1.0)) : 0.0;

@@ -1,0 +1,94 @@
+"""ctypes view of libpgsgd.so (include/pgsgd.h). Argument marshalling only."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+import threading
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+P = C.c_void_p
+u8, u32, u64, i32, i64, dbl = C.c_uint8, C.c_uint32, C.c_uint64, C.c_int, C.c_int64, C.c_double
+
+PGSGD_OK, PGSGD_EINVAL, PGSGD_ERANGE, PGSGD_ENOMEM, PGSGD_ECUDA, PGSGD_ETIMEOUT, PGSGD_EDEVICE = range(7)
+
+OPT = dict(coord_mode=1, updates_per_step=2, block=3, blocks_per_sm=4, updates_per_thread=5,
+           atomic_updates=6, rebase=7, timing=8, max_concurrent=9)
+
+
+class StressResult(C.Structure):
+    _fields_ = [("mean", dbl), ("stddev", dbl), ("ci_lo", dbl), ("ci_hi", dbl),
+                ("n_valid", u64), ("n_skipped", u64)]
+
+
+class Info(C.Structure):
+    _fields_ = [("n_steps", u64), ("device_bytes", u64), ("max_path_steps", u64),
+                ("max_path_nt", i64), ("n_nodes", u32), ("n_paths", u32), ("device", C.c_int32),
+                ("sm_count", C.c_int32)]
+
+
+class PgsgdError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{status_name(status)}: {message}")
+        self.status = status
+
+
+_SIGS = {
+    "pgsgd_create": ([P, u32, P, u32, P, P, P, i32, P, P], i32),
+    "pgsgd_destroy": ([P], i32),
+    "pgsgd_set_option": ([P, i32, i64], i32),
+    "pgsgd_get_option": ([P, i32, P], i32),
+    "pgsgd_info_get": ([P, P], i32),
+    "pgsgd_set_coords": ([P, P, i32, P], i32),
+    "pgsgd_get_coords": ([P, P, i32, P], i32),
+    "pgsgd_layout": ([P, u32, P, dbl, dbl, dbl, u64, u32, u32, P], i32),
+    "pgsgd_stress": ([P, u32, u64, P, P, P], i32),
+    "pgsgd_debug_sample": ([P, u32, u32, dbl, u64, u64, u64, P, P], i32),
+    "pgsgd_debug_sweep": ([P, u32, u32, dbl, dbl, u64, u64, u64, P, P], i32),
+    "pgsgd_timing_read": ([P, P, P, P, i32], i32),
+    "pgsgd_last_error": ([], C.c_char_p),
+    "pgsgd_status_string": ([i32], C.c_char_p),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libpgsgd.so from the package's build folder (building it if stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_missing else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"libpgsgd.so not built at {path}")
+            lib = C.CDLL(path)
+            for name, (args, res) in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = lib
+    return _lib
+
+
+def status_name(status: int) -> str:
+    return load().pgsgd_status_string(int(status)).decode()
+
+
+def check(status: int):
+    if status != PGSGD_OK:
+        raise PgsgdError(status, load().pgsgd_last_error().decode())
+
+
+def declared_symbols(header: str | None = None):
+    """Function names the public header declares."""
+    if header is None:
+        header = os.path.join(_build.ROOT, "include", "pgsgd.h")
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pgsgd_[a-z_]+)\s*\(", text)))

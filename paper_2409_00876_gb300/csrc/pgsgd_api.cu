@@ -1,0 +1,641 @@
+// C ABI of libpgsgd.so (declared in include/pgsgd.h): graph handle,
+// validation, device memory ownership, the iteration loop of Algorithm 1
+// and the sampled-stress reduction. Host code only; kernels live in
+// pgsgd_kernels.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pgsgd.h"
+#include "pgsgd_internal.h"
+
+using namespace pgsgd;
+
+struct pgsgd_graph {
+    int device = 0;
+    int sm_count = 0;
+    uint32_t n_nodes = 0, n_paths = 0;
+    uint64_t n_steps = 0;
+    uint64_t max_path_steps = 0;
+    int64_t max_path_nt = 0;
+    std::vector<uint64_t> h_path_off;
+
+    NodeRec* d_nodes = nullptr;
+    uint64_t* d_steps = nullptr;
+    uint64_t* d_path_off = nullptr;
+    uint64_t* d_sample_off = nullptr;  // stress sample offsets [P + 1]
+    float* d_zipf_B = nullptr;
+    uint32_t* d_flags = nullptr;
+    double* d_partials = nullptr;      // stress scratch [max_stress_blocks][3] + 3 totals
+    double* d_per_path = nullptr;      // [P][3]
+    double* d_xy = nullptr;            // coordinate staging [V][4]
+    void* d_debug = nullptr;           // debug output staging
+    size_t debug_bytes = 0;
+    int max_stress_blocks = 0;
+    uint64_t stress_samples_per_step = 0;
+
+    bool has_coords = false;
+    float zipf_theta = NAN;
+
+    // options
+    int coord_mode = 0;
+    int updates_per_step = 10;
+    int block = 256;
+    int blocks_per_sm = 8;
+    int upt = 2;
+    int atomic = 0;
+    int rebase = 1;
+    int timing = 0;
+    int64_t max_concurrent = -1;  // -1 = automatic
+
+    // timing
+    std::vector<cudaEvent_t> ev_free;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+    double timing_ms = 0.0;
+    uint64_t timing_launches = 0, timing_updates = 0;
+
+    uint64_t device_bytes = 0;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int status, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return status;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(e == cudaErrorMemoryAllocation ? PGSGD_ENOMEM : PGSGD_ECUDA, "%s: %s (%s)", what,
+                cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+#define CK(call, what)                                       \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what);   \
+    } while (0)
+
+cudaStream_t S(void* s) { return static_cast<cudaStream_t>(s); }
+
+template <class T>
+cudaError_t dalloc(pgsgd_graph* g, T** p, size_t count) {
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+    if (e == cudaSuccess) g->device_bytes += count * sizeof(T);
+    return e;
+}
+
+void free_graph(pgsgd_graph* g) {
+    if (!g) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(g->device);
+    cudaFree(g->d_nodes);
+    cudaFree(g->d_steps);
+    cudaFree(g->d_path_off);
+    cudaFree(g->d_sample_off);
+    cudaFree(g->d_zipf_B);
+    cudaFree(g->d_flags);
+    cudaFree(g->d_partials);
+    cudaFree(g->d_per_path);
+    cudaFree(g->d_xy);
+    cudaFree(g->d_debug);
+    for (auto& pr : g->ev_pending) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    for (auto e : g->ev_free) cudaEventDestroy(e);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete g;
+}
+
+const char* flag_text(uint32_t f) {
+    if (f & FLAG_BAD_NODE) return "a step's node id is >= n_nodes";
+    if (f & FLAG_BAD_REV) return "a step's orientation is not 0 or 1";
+    if (f & FLAG_ZERO_LEN) return "a node has length 0";
+    if (f & FLAG_BAD_POS) return "step positions do not start at 0 or do not advance by node length";
+    if (f & FLAG_COORD_NAN) return "a coordinate is not finite";
+    return "unknown";
+}
+
+// Read and clear the device flag word.
+int check_flags(pgsgd_graph* g, cudaStream_t st, const char* what) {
+    uint32_t f = 0;
+    CK(cudaMemcpyAsync(&f, g->d_flags, sizeof f, cudaMemcpyDeviceToHost, st), "flag readback");
+    CK(cudaStreamSynchronize(st), "flag sync");
+    if (f) {
+        CK(cudaMemsetAsync(g->d_flags, 0, sizeof(uint32_t), st), "flag clear");
+        CK(cudaStreamSynchronize(st), "flag clear sync");
+        if (f & (FLAG_POS_RANGE | FLAG_COORD_RANGE))
+            return fail(PGSGD_ERANGE, "%s: %s", what,
+                        (f & FLAG_POS_RANGE) ? "a step position is outside [0, 2^32)"
+                                             : "a coordinate magnitude is >= 2^30 (anchored mode)");
+        return fail(PGSGD_EINVAL, "%s: %s", what, flag_text(f));
+    }
+    return PGSGD_OK;
+}
+
+int ensure_zipf(pgsgd_graph* g, float theta, cudaStream_t st) {
+    if (g->zipf_theta == theta) return PGSGD_OK;
+    CK(launch_zipf_setup(g->d_path_off, g->n_paths, theta, g->d_zipf_B, nullptr, st), "zipf setup");
+    g->zipf_theta = theta;
+    return PGSGD_OK;
+}
+
+SamplerArgs sampler_args(const pgsgd_graph* g, uint32_t T, uint32_t t, float theta, uint64_t seed) {
+    SamplerArgs a;
+    a.steps = g->d_steps;
+    a.path_off = g->d_path_off;
+    a.zipf_B = g->d_zipf_B;
+    a.n_steps = g->n_steps;
+    a.n_paths = g->n_paths;
+    a.T = T;
+    a.t = t;
+    a.key0 = (uint32_t)seed;
+    a.key1 = (uint32_t)(seed >> 32);
+    a.zc.theta = theta;
+    a.zc.omt = a.zc.A = a.zc.s = 0.0f;
+    return a;
+}
+
+int ensure_debug(pgsgd_graph* g, size_t bytes) {
+    if (g->debug_bytes >= bytes) return PGSGD_OK;
+    if (g->d_debug) {
+        cudaFree(g->d_debug);
+        g->device_bytes -= g->debug_bytes;
+        g->d_debug = nullptr;
+        g->debug_bytes = 0;
+    }
+    CK(cudaMalloc(&g->d_debug, bytes), "debug buffer");
+    g->debug_bytes = bytes;
+    g->device_bytes += bytes;
+    return PGSGD_OK;
+}
+
+int check_theta(double theta) {
+    if (!(theta >= 0.0 && theta <= 4.0)) return fail(PGSGD_EINVAL, "theta %g outside [0, 4]", theta);
+    return PGSGD_OK;
+}
+
+cudaEvent_t take_event(pgsgd_graph* g) {
+    if (!g->ev_free.empty()) {
+        cudaEvent_t e = g->ev_free.back();
+        g->ev_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pgsgd_last_error(void) { return g_last_error.c_str(); }
+
+const char* pgsgd_status_string(int status) {
+    switch (status) {
+        case PGSGD_OK: return "PGSGD_OK";
+        case PGSGD_EINVAL: return "PGSGD_EINVAL";
+        case PGSGD_ERANGE: return "PGSGD_ERANGE";
+        case PGSGD_ENOMEM: return "PGSGD_ENOMEM";
+        case PGSGD_ECUDA: return "PGSGD_ECUDA";
+        case PGSGD_ETIMEOUT: return "PGSGD_ETIMEOUT";
+        case PGSGD_EDEVICE: return "PGSGD_EDEVICE";
+        default: return "PGSGD_UNKNOWN";
+    }
+}
+
+int pgsgd_create(const uint32_t* node_len, uint32_t n_nodes, const uint64_t* path_off,
+                 uint32_t n_paths, const uint32_t* step_node, const uint8_t* step_rev,
+                 const int64_t* step_pos, int on_device, void* cuda_stream, pgsgd_graph** out) {
+    g_last_error.clear();
+    if (!out) return fail(PGSGD_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!node_len || !path_off) return fail(PGSGD_EINVAL, "node_len and path_off are required");
+    if (n_nodes == 0) return fail(PGSGD_EINVAL, "n_nodes is 0");
+    if (n_nodes >= (1u << 31)) return fail(PGSGD_ERANGE, "n_nodes %u >= 2^31", n_nodes);
+    if (n_paths == 0) return fail(PGSGD_EINVAL, "n_paths is 0");
+    if (n_paths > kMaxPaths) return fail(PGSGD_ERANGE, "n_paths %u > %u", n_paths, kMaxPaths);
+    if (on_device != 0 && on_device != 1) return fail(PGSGD_EINVAL, "on_device must be 0 or 1");
+    cudaStream_t st = S(cuda_stream);
+
+    // The path table is small: validate it on the host.
+    std::vector<uint64_t> off(n_paths + 1);
+    if (on_device) {
+        CK(cudaMemcpy(off.data(), path_off, off.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost),
+           "path_off readback");
+    } else {
+        std::memcpy(off.data(), path_off, off.size() * sizeof(uint64_t));
+    }
+    if (off[0] != 0) return fail(PGSGD_EINVAL, "path_off[0] = %llu, must be 0", (unsigned long long)off[0]);
+    uint64_t max_steps = 0;
+    for (uint32_t p = 0; p < n_paths; ++p) {
+        if (off[p + 1] < off[p]) return fail(PGSGD_EINVAL, "path_off decreases at path %u", p);
+        max_steps = std::max<uint64_t>(max_steps, off[p + 1] - off[p]);
+    }
+    const uint64_t S_ = off[n_paths];
+    if (S_ > 0 && (!step_node || !step_rev || !step_pos))
+        return fail(PGSGD_EINVAL, "step arrays are required when the paths have steps");
+
+    pgsgd_graph* g = new (std::nothrow) pgsgd_graph();
+    if (!g) return fail(PGSGD_ENOMEM, "host allocation");
+    cudaError_t e = cudaGetDevice(&g->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, g->device);
+    if (e != cudaSuccess) {
+        delete g;
+        return cuda_fail(e, "device query");
+    }
+    g->n_nodes = n_nodes;
+    g->n_paths = n_paths;
+    g->n_steps = S_;
+    g->max_path_steps = max_steps;
+    g->h_path_off = off;
+
+    int rc = PGSGD_OK;
+    uint32_t* t_len = nullptr;
+    uint32_t* t_node = nullptr;
+    uint8_t* t_rev = nullptr;
+    int64_t* t_pos = nullptr;
+    std::vector<int64_t> nt(n_paths);
+    int64_t* d_nt = nullptr;
+    do {
+#define TRY(call, what)                        \
+    {                                          \
+        cudaError_t e_ = (call);               \
+        if (e_ != cudaSuccess) {               \
+            rc = cuda_fail(e_, what);          \
+            break;                             \
+        }                                      \
+    }
+        TRY(dalloc(g, &g->d_nodes, n_nodes), "node records");
+        TRY(dalloc(g, &g->d_steps, S_), "step records");
+        TRY(dalloc(g, &g->d_path_off, n_paths + 1), "path table");
+        TRY(dalloc(g, &g->d_sample_off, n_paths + 1), "stress sample table");
+        TRY(dalloc(g, &g->d_zipf_B, n_paths), "zipf table");
+        TRY(dalloc(g, &g->d_flags, 1), "flags");
+        g->max_stress_blocks = g->sm_count * 8;
+        TRY(dalloc(g, &g->d_partials, 3 * (size_t)g->max_stress_blocks + 3), "stress scratch");
+        TRY(dalloc(g, &g->d_per_path, 3 * (size_t)n_paths), "per-path stress");
+        TRY(cudaMemsetAsync(g->d_flags, 0, sizeof(uint32_t), st), "flags clear");
+        TRY(cudaMemcpyAsync(g->d_path_off, off.data(), off.size() * sizeof(uint64_t),
+                            cudaMemcpyHostToDevice, st), "path table upload");
+        const uint32_t* src_len = node_len;
+        const uint32_t* src_node = step_node;
+        const uint8_t* src_rev = step_rev;
+        const int64_t* src_pos = step_pos;
+        if (!on_device) {
+            TRY(cudaMalloc(&t_len, (size_t)n_nodes * 4), "staging");
+            TRY(cudaMemcpyAsync(t_len, node_len, (size_t)n_nodes * 4, cudaMemcpyHostToDevice, st), "upload");
+            src_len = t_len;
+            if (S_) {
+                TRY(cudaMalloc(&t_node, S_ * 4), "staging");
+                TRY(cudaMalloc(&t_rev, S_), "staging");
+                TRY(cudaMalloc(&t_pos, S_ * 8), "staging");
+                TRY(cudaMemcpyAsync(t_node, step_node, S_ * 4, cudaMemcpyHostToDevice, st), "upload");
+                TRY(cudaMemcpyAsync(t_rev, step_rev, S_, cudaMemcpyHostToDevice, st), "upload");
+                TRY(cudaMemcpyAsync(t_pos, step_pos, S_ * 8, cudaMemcpyHostToDevice, st), "upload");
+                src_node = t_node;
+                src_rev = t_rev;
+                src_pos = t_pos;
+            }
+        }
+        TRY(launch_pack_nodes(src_len, n_nodes, g->d_nodes, g->d_flags, g->sm_count, st), "pack nodes");
+        TRY(launch_pack_steps(src_node, src_rev, src_pos, src_len, n_nodes, g->d_path_off, n_paths, S_,
+                              g->d_steps, g->d_flags, g->sm_count, st), "pack steps");
+        rc = check_flags(g, st, "pgsgd_create");
+        if (rc) break;
+        TRY(cudaMalloc(&d_nt, (size_t)n_paths * 8), "extent buffer");
+        TRY(launch_path_extent(g->d_steps, g->d_path_off, g->d_nodes, n_paths, d_nt, st), "path extent");
+        TRY(cudaMemcpyAsync(nt.data(), d_nt, (size_t)n_paths * 8, cudaMemcpyDeviceToHost, st), "extent readback");
+        TRY(cudaStreamSynchronize(st), "create sync");
+        for (int64_t v : nt) g->max_path_nt = std::max(g->max_path_nt, v);
+#undef TRY
+    } while (0);
+    cudaFree(t_len);
+    cudaFree(t_node);
+    cudaFree(t_rev);
+    cudaFree(t_pos);
+    cudaFree(d_nt);
+    if (rc != PGSGD_OK) {
+        cudaStreamSynchronize(st);
+        free_graph(g);
+        return rc;
+    }
+    *out = g;
+    return PGSGD_OK;
+}
+
+int pgsgd_destroy(pgsgd_graph* g) {
+    free_graph(g);
+    return PGSGD_OK;
+}
+
+int pgsgd_set_option(pgsgd_graph* g, int option, int64_t v) {
+    if (!g) return fail(PGSGD_EINVAL, "graph is NULL");
+    switch (option) {
+        case PGSGD_OPT_COORD_MODE:
+            if (v != 0 && v != 1) return fail(PGSGD_EINVAL, "coord mode must be 0 or 1");
+            g->coord_mode = (int)v;
+            g->has_coords = false;
+            return PGSGD_OK;
+        case PGSGD_OPT_UPDATES_PER_STEP:
+            if (v < 1 || v > 1000) return fail(PGSGD_EINVAL, "updates per step must be in [1, 1000]");
+            g->updates_per_step = (int)v;
+            return PGSGD_OK;
+        case PGSGD_OPT_BLOCK:
+            if (v < 64 || v > 1024 || v % 32) return fail(PGSGD_EINVAL, "block must be 64..1024, multiple of 32");
+            g->block = (int)v;
+            return PGSGD_OK;
+        case PGSGD_OPT_BLOCKS_PER_SM:
+            if (v < 1 || v > 64) return fail(PGSGD_EINVAL, "blocks per SM must be in [1, 64]");
+            g->blocks_per_sm = (int)v;
+            return PGSGD_OK;
+        case PGSGD_OPT_UPDATES_PER_THREAD:
+            if (v != 1 && v != 2 && v != 4) return fail(PGSGD_EINVAL, "updates per thread must be 1, 2 or 4");
+            g->upt = (int)v;
+            return PGSGD_OK;
+        case PGSGD_OPT_ATOMIC_UPDATES:
+            g->atomic = v ? 1 : 0;
+            return PGSGD_OK;
+        case PGSGD_OPT_REBASE:
+            g->rebase = v ? 1 : 0;
+            return PGSGD_OK;
+        case PGSGD_OPT_TIMING:
+            g->timing = v ? 1 : 0;
+            return PGSGD_OK;
+        case PGSGD_OPT_MAX_CONCURRENT:
+            if (v < -1) return fail(PGSGD_EINVAL, "max concurrent must be >= -1");
+            g->max_concurrent = v;
+            return PGSGD_OK;
+        default:
+            return fail(PGSGD_EINVAL, "unknown option %d", option);
+    }
+}
+
+int pgsgd_get_option(const pgsgd_graph* g, int option, int64_t* v) {
+    if (!g || !v) return fail(PGSGD_EINVAL, "NULL argument");
+    switch (option) {
+        case PGSGD_OPT_COORD_MODE: *v = g->coord_mode; return PGSGD_OK;
+        case PGSGD_OPT_UPDATES_PER_STEP: *v = g->updates_per_step; return PGSGD_OK;
+        case PGSGD_OPT_BLOCK: *v = g->block; return PGSGD_OK;
+        case PGSGD_OPT_BLOCKS_PER_SM: *v = g->blocks_per_sm; return PGSGD_OK;
+        case PGSGD_OPT_UPDATES_PER_THREAD: *v = g->upt; return PGSGD_OK;
+        case PGSGD_OPT_ATOMIC_UPDATES: *v = g->atomic; return PGSGD_OK;
+        case PGSGD_OPT_REBASE: *v = g->rebase; return PGSGD_OK;
+        case PGSGD_OPT_TIMING: *v = g->timing; return PGSGD_OK;
+        case PGSGD_OPT_MAX_CONCURRENT: *v = g->max_concurrent; return PGSGD_OK;
+        default: return fail(PGSGD_EINVAL, "unknown option %d", option);
+    }
+}
+
+int pgsgd_info_get(const pgsgd_graph* g, pgsgd_info* out) {
+    if (!g || !out) return fail(PGSGD_EINVAL, "NULL argument");
+    out->n_steps = g->n_steps;
+    out->device_bytes = g->device_bytes;
+    out->max_path_steps = g->max_path_steps;
+    out->max_path_nt = g->max_path_nt;
+    out->n_nodes = g->n_nodes;
+    out->n_paths = g->n_paths;
+    out->device = g->device;
+    out->sm_count = g->sm_count;
+    return PGSGD_OK;
+}
+
+int pgsgd_set_coords(pgsgd_graph* g, const double* xy, int on_device, void* cuda_stream) {
+    if (!g || !xy) return fail(PGSGD_EINVAL, "NULL argument");
+    cudaStream_t st = S(cuda_stream);
+    const size_t bytes = (size_t)g->n_nodes * 4 * sizeof(double);
+    const double* src = xy;
+    if (!on_device) {
+        if (!g->d_xy) CK(dalloc(g, &g->d_xy, (size_t)g->n_nodes * 4), "coordinate staging");
+        CK(cudaMemcpyAsync(g->d_xy, xy, bytes, cudaMemcpyHostToDevice, st), "coordinate upload");
+        src = g->d_xy;
+    }
+    CK(launch_set_coords(src, g->d_nodes, g->n_nodes, g->coord_mode == 0, g->d_flags, g->sm_count, st),
+       "set coords");
+    int rc = check_flags(g, st, "pgsgd_set_coords");
+    if (rc) return rc;
+    g->has_coords = true;
+    return PGSGD_OK;
+}
+
+int pgsgd_get_coords(pgsgd_graph* g, double* xy, int on_device, void* cuda_stream) {
+    if (!g || !xy) return fail(PGSGD_EINVAL, "NULL argument");
+    if (!g->has_coords) return fail(PGSGD_EINVAL, "no layout: call pgsgd_set_coords first");
+    cudaStream_t st = S(cuda_stream);
+    const size_t bytes = (size_t)g->n_nodes * 4 * sizeof(double);
+    if (on_device) {
+        CK(launch_get_coords(g->d_nodes, xy, g->n_nodes, g->sm_count, st), "get coords");
+        return PGSGD_OK;
+    }
+    if (!g->d_xy) CK(dalloc(g, &g->d_xy, (size_t)g->n_nodes * 4), "coordinate staging");
+    CK(launch_get_coords(g->d_nodes, g->d_xy, g->n_nodes, g->sm_count, st), "get coords");
+    CK(cudaMemcpyAsync(xy, g->d_xy, bytes, cudaMemcpyDeviceToHost, st), "coordinate download");
+    CK(cudaStreamSynchronize(st), "coordinate sync");
+    return PGSGD_OK;
+}
+
+int pgsgd_layout(pgsgd_graph* g, uint32_t iter_max, const double* eta, double eta_max, double eta_min,
+                 double theta, uint64_t seed, uint32_t iter_begin, uint32_t iter_end, void* cuda_stream) {
+    if (!g) return fail(PGSGD_EINVAL, "graph is NULL");
+    if (!g->has_coords) return fail(PGSGD_EINVAL, "no layout: call pgsgd_set_coords first");
+    if (iter_max == 0) return fail(PGSGD_EINVAL, "iter_max is 0");
+    if (iter_begin > iter_end || iter_end > iter_max)
+        return fail(PGSGD_EINVAL, "need iter_begin <= iter_end <= iter_max");
+    int rc = check_theta(theta);
+    if (rc) return rc;
+    cudaStream_t st = S(cuda_stream);
+    // learning rate (Algorithm 1, line 3): Zheng et al.'s exponential annealing
+    std::vector<double> sched(iter_max);
+    if (eta) {
+        for (uint32_t t = 0; t < iter_max; ++t) sched[t] = eta[t];
+    } else {
+        const double emax = eta_max > 0 ? eta_max : (double)g->max_path_nt * (double)g->max_path_nt;
+        const double emin = eta_min > 0 ? eta_min : 0.01;
+        if (!(emax > 0)) return fail(PGSGD_EINVAL, "eta_max must be positive");
+        if (iter_max == 1) {
+            sched[0] = emax;
+        } else {
+            const double lambda = std::log(emax / emin) / (double)(iter_max - 1);
+            for (uint32_t t = 0; t < iter_max; ++t) sched[t] = emax * std::exp(-lambda * (double)t);
+        }
+    }
+    const float th = (float)theta;
+    rc = ensure_zipf(g, th, st);
+    if (rc) return rc;
+    const uint64_t N = (uint64_t)g->updates_per_step * g->n_steps;
+    // grid: a multiple of the SM count, capped by the concurrency limit
+    const int per_sm = g->blocks_per_sm;
+    int grid = g->sm_count * per_sm;
+    int64_t cap = g->max_concurrent;
+    if (cap == -1) cap = std::max<int64_t>(2048, (int64_t)g->n_nodes / 2);
+    if (cap > 0) {
+        const int64_t per_block = (int64_t)g->block * g->upt;
+        const int64_t gmax = std::max<int64_t>(1, cap / per_block);
+        if (gmax < grid) grid = (int)gmax;
+    }
+    UpdateLaunch L;
+    L.nodes = g->d_nodes;
+    L.u_begin = 0;
+    L.n_updates = N;
+    L.block = g->block;
+    L.grid = grid;
+    L.upt = g->upt;
+    L.atomic = g->atomic != 0;
+    for (uint32_t t = iter_begin; t < iter_end; ++t) {
+        L.s = sampler_args(g, iter_max, t, th, seed);
+        L.eta = (float)sched[t];
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (g->timing) {
+            e0 = take_event(g);
+            e1 = take_event(g);
+            CK(cudaEventRecord(e0, st), "timing event");
+        }
+        CK(launch_update(L, st), "update kernel");
+        if (g->timing) {
+            CK(cudaEventRecord(e1, st), "timing event");
+            g->ev_pending.emplace_back(e0, e1);
+            g->timing_launches += 1;
+            g->timing_updates += N;
+        }
+        if (g->rebase && g->coord_mode == 0) CK(launch_rebase(g->d_nodes, g->n_nodes, g->sm_count, st), "rebase");
+    }
+    return PGSGD_OK;
+}
+
+int pgsgd_timing_read(pgsgd_graph* g, double* total_ms, uint64_t* launches, uint64_t* updates, int reset) {
+    if (!g) return fail(PGSGD_EINVAL, "graph is NULL");
+    for (auto& pr : g->ev_pending) {
+        CK(cudaEventSynchronize(pr.second), "timing sync");
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, pr.first, pr.second), "timing read");
+        g->timing_ms += ms;
+        g->ev_free.push_back(pr.first);
+        g->ev_free.push_back(pr.second);
+    }
+    g->ev_pending.clear();
+    if (total_ms) *total_ms = g->timing_ms;
+    if (launches) *launches = g->timing_launches;
+    if (updates) *updates = g->timing_updates;
+    if (reset) {
+        g->timing_ms = 0.0;
+        g->timing_launches = 0;
+        g->timing_updates = 0;
+    }
+    return PGSGD_OK;
+}
+
+int pgsgd_stress(pgsgd_graph* g, uint32_t samples_per_step, uint64_t seed, pgsgd_stress_result* out,
+                 double* per_path, void* cuda_stream) {
+    if (!g || !out) return fail(PGSGD_EINVAL, "NULL argument");
+    if (!g->has_coords) return fail(PGSGD_EINVAL, "no layout: call pgsgd_set_coords first");
+    if (samples_per_step == 0) return fail(PGSGD_EINVAL, "samples_per_step is 0");
+    cudaStream_t st = S(cuda_stream);
+    uint64_t n_samples = 0;
+    if (g->stress_samples_per_step != samples_per_step) {
+        std::vector<uint64_t> so(g->n_paths + 1, 0);
+        for (uint32_t p = 0; p < g->n_paths; ++p) {
+            const uint64_t n = g->h_path_off[p + 1] - g->h_path_off[p];
+            so[p + 1] = so[p] + (n >= 2 ? (uint64_t)samples_per_step * n : 0);
+        }
+        CK(cudaMemcpyAsync(g->d_sample_off, so.data(), so.size() * 8, cudaMemcpyHostToDevice, st),
+           "sample table upload");
+        CK(cudaStreamSynchronize(st), "sample table sync");
+        g->stress_samples_per_step = samples_per_step;
+    }
+    for (uint32_t p = 0; p < g->n_paths; ++p) {
+        const uint64_t n = g->h_path_off[p + 1] - g->h_path_off[p];
+        if (n >= 2) n_samples += (uint64_t)samples_per_step * n;
+    }
+    StressLaunch L;
+    L.steps = g->d_steps;
+    L.path_off = g->d_path_off;
+    L.sample_off = g->d_sample_off;
+    L.nodes = g->d_nodes;
+    L.n_samples = n_samples;
+    L.n_paths = g->n_paths;
+    L.key0 = (uint32_t)seed;
+    L.key1 = (uint32_t)(seed >> 32);
+    L.partials = g->d_partials;
+    L.per_path = per_path ? g->d_per_path : nullptr;
+    L.block = 256;
+    const uint64_t want = (n_samples + 2 * 256 - 1) / (2 * 256);
+    L.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)g->max_stress_blocks));
+    if (per_path) CK(cudaMemsetAsync(g->d_per_path, 0, (size_t)g->n_paths * 3 * 8, st), "per-path clear");
+    CK(launch_stress(L, st), "stress kernel");
+    double* tot = g->d_partials + 3 * (size_t)g->max_stress_blocks;
+    CK(launch_stress_finalize(g->d_partials, L.grid, tot, st), "stress finalize");
+    double h[3];
+    CK(cudaMemcpyAsync(h, tot, sizeof h, cudaMemcpyDeviceToHost, st), "stress readback");
+    if (per_path)
+        CK(cudaMemcpyAsync(per_path, g->d_per_path, (size_t)g->n_paths * 3 * 8, cudaMemcpyDeviceToHost, st),
+           "per-path readback");
+    CK(cudaStreamSynchronize(st), "stress sync");
+    const double n = h[2];
+    const double mean = n > 0 ? h[0] / n : 0.0;
+    const double var = n > 1 ? std::max(0.0, (h[1] - n * mean * mean) / (n - 1.0)) : 0.0;
+    const double sd = std::sqrt(var);
+    const double half = n > 0 ? 1.96 * sd / std::sqrt(n) : 0.0;
+    out->mean = mean;
+    out->stddev = sd;
+    out->ci_lo = mean - half;
+    out->ci_hi = mean + half;
+    out->n_valid = (uint64_t)n;
+    out->n_skipped = n_samples - (uint64_t)n;
+    return PGSGD_OK;
+}
+
+int pgsgd_debug_sample(pgsgd_graph* g, uint32_t t, uint32_t iter_max, double theta, uint64_t seed,
+                       uint64_t u_begin, uint64_t count, pgsgd_sample* out, void* cuda_stream) {
+    if (!g || (!out && count)) return fail(PGSGD_EINVAL, "NULL argument");
+    if (iter_max == 0 || t >= iter_max) return fail(PGSGD_EINVAL, "need t < iter_max");
+    int rc = check_theta(theta);
+    if (rc) return rc;
+    if (count == 0) return PGSGD_OK;
+    cudaStream_t st = S(cuda_stream);
+    rc = ensure_zipf(g, (float)theta, st);
+    if (rc) return rc;
+    rc = ensure_debug(g, count * sizeof(pgsgd_sample));
+    if (rc) return rc;
+    CK(launch_debug_sample(sampler_args(g, iter_max, t, (float)theta, seed), u_begin, count, g->d_nodes,
+                           g->d_debug, g->sm_count, st), "debug sample");
+    CK(cudaMemcpyAsync(out, g->d_debug, count * sizeof(pgsgd_sample), cudaMemcpyDeviceToHost, st),
+       "debug readback");
+    CK(cudaStreamSynchronize(st), "debug sync");
+    return PGSGD_OK;
+}
+
+int pgsgd_debug_sweep(pgsgd_graph* g, uint32_t t, uint32_t iter_max, double eta, double theta,
+                      uint64_t seed, uint64_t u_begin, uint64_t count, float* out, void* cuda_stream) {
+    if (!g || (!out && count)) return fail(PGSGD_EINVAL, "NULL argument");
+    if (!g->has_coords) return fail(PGSGD_EINVAL, "no layout: call pgsgd_set_coords first");
+    if (iter_max == 0 || t >= iter_max) return fail(PGSGD_EINVAL, "need t < iter_max");
+    int rc = check_theta(theta);
+    if (rc) return rc;
+    if (count == 0) return PGSGD_OK;
+    cudaStream_t st = S(cuda_stream);
+    rc = ensure_zipf(g, (float)theta, st);
+    if (rc) return rc;
+    rc = ensure_debug(g, count * sizeof(float4));
+    if (rc) return rc;
+    CK(launch_debug_sweep(sampler_args(g, iter_max, t, (float)theta, seed), u_begin, count, g->d_nodes,
+                          (float)eta, static_cast<float4*>(g->d_debug), g->sm_count, st), "debug sweep");
+    CK(cudaMemcpyAsync(out, g->d_debug, count * sizeof(float4), cudaMemcpyDeviceToHost, st), "sweep readback");
+    CK(cudaStreamSynchronize(st), "sweep sync");
+    return PGSGD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,307 @@
+// Device-side building blocks of the PG-SGD path: the packed records, the
+// Philox4x32-10 generator, binary32 elementary functions with a fixed
+// operation order, the Zipf rejection-inversion sampler and the per-update
+// pair draw of Algorithm 1 (Section II-C, lines 5-13).
+//
+// Every floating-point operation that decides an integer (the Zipf draw) is
+// written with explicit round-to-nearest intrinsics (__fadd_rn, __fmul_rn,
+// __fdiv_rn, ...), which the compiler never contracts into fused
+// multiply-adds, so the draw is the same on every run and matches the
+// sampler definition operation for operation.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pgsgd {
+
+// ---------------------------------------------------------------- records
+
+// One node of the layout: the two endpoints of its segment (Section II-C:
+// a node is drawn as a line segment) as FP32 offsets from an integer anchor
+// per axis, plus the sequence length the reference distances need. 32 bytes,
+// 32-byte aligned: one DRAM sector holds a whole node (the cache-friendly
+// node record of Section IV-B1, sized to a Blackwell sector).
+struct __align__(32) NodeRec {
+    float sx, sy, ex, ey;  // start x, start y, end x, end y (offsets)
+    int32_t ax, ay;        // anchors (0 in plain-FP32 mode)
+    uint32_t len;          // sequence length in nucleotides
+    uint32_t pad;
+};
+static_assert(sizeof(NodeRec) == 32, "node record must fill one sector");
+
+// One path step packed in 64 bits: node id (bits 0-30), orientation (bit 31),
+// nucleotide position where the path enters the step (bits 32-63).
+__host__ __device__ __forceinline__ uint64_t pack_step(uint32_t node, uint32_t rev, uint64_t pos) {
+    return (uint64_t)node | ((uint64_t)(rev & 1u) << 31) | (pos << 32);
+}
+__device__ __forceinline__ uint32_t step_node(uint64_t s) { return (uint32_t)s & 0x7fffffffu; }
+__device__ __forceinline__ uint32_t step_rev(uint64_t s) { return ((uint32_t)s >> 31) & 1u; }
+__device__ __forceinline__ int64_t step_pos(uint64_t s) { return (int64_t)(s >> 32); }
+
+// Path position of endpoint e (0 = start point, 1 = end point) of a step: a
+// step taken in reverse meets its node's end point first.
+__device__ __forceinline__ int64_t endpoint_pos(uint64_t s, uint32_t e, uint32_t len) {
+    return step_pos(s) + (((e ^ step_rev(s)) & 1u) ? (int64_t)len : 0);
+}
+
+// ---------------------------------------------------------------- memory access
+
+// Packed step records are read-only during a launch: non-coherent path.
+__device__ __forceinline__ uint64_t load_step(const uint64_t* p) {
+    return __ldg(reinterpret_cast<const unsigned long long*>(p));
+}
+
+// Node records change during a launch (Hogwild!): read them from L2 (.cg),
+// never from a possibly stale L1 line, with one 256-bit load per node.
+__device__ __forceinline__ NodeRec load_node(const NodeRec* p) {
+    NodeRec r;
+    uint32_t a0, a1, a2, a3, a4, a5, a6, a7;
+    asm volatile("ld.global.cg.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(a0), "=r"(a1), "=r"(a2), "=r"(a3), "=r"(a4), "=r"(a5), "=r"(a6), "=r"(a7)
+                 : "l"(p));
+    r.sx = __uint_as_float(a0); r.sy = __uint_as_float(a1);
+    r.ex = __uint_as_float(a2); r.ey = __uint_as_float(a3);
+    r.ax = (int32_t)a4; r.ay = (int32_t)a5; r.len = a6; r.pad = a7;
+    return r;
+}
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3"
+// (SC'11): ten rounds of two 32x32->64 multiplies with a Weyl key schedule.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi_a = __umulhi(0xD2511F53u, c.x), lo_a = 0xD2511F53u * c.x;
+        const uint32_t hi_b = __umulhi(0xCD9E8D57u, c.z), lo_b = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi_b ^ c.y ^ k0, lo_b, hi_a ^ c.w ^ k1, lo_a);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// High 64 bits of a 64x64 product: a uniform 64-bit word mapped onto [0, n).
+__device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) { return __umul64hi(a, b); }
+
+// ---------------------------------------------------------------- binary32 math
+// ln: x = 2^e m with m in [sqrt(1/2), sqrt(2)), ln m = 2 atanh(s),
+// s = (m - 1) / (m + 1), odd series to s^11; exp: y = n ln2 + r with a
+// two-part ln2 (Cody and Waite), Taylor polynomial of degree 7 for e^r.
+
+#define PG_LN2_HI 0x1.62e4p-1f
+#define PG_LN2_LO 0x1.7f7d1cp-20f
+#define PG_INV_LN2 0x1.715476p+0f
+#define PG_SQRT2 0x1.6a09e6p+0f
+
+__device__ __forceinline__ float f_ln(float x) {
+    const uint32_t b = __float_as_uint(x);
+    int e = (int)((b >> 23) & 0xffu) - 127;
+    float m = __uint_as_float((b & 0x7fffffu) | 0x3f800000u);
+    if (m > PG_SQRT2) { m = __fmul_rn(m, 0.5f); e = e + 1; }
+    const float f = __fsub_rn(m, 1.0f);
+    const float s = __fdiv_rn(f, __fadd_rn(2.0f, f));
+    const float z = __fmul_rn(s, s);
+    float p = 0x1.745d18p-4f;
+    p = __fadd_rn(__fmul_rn(p, z), 0x1.c71c72p-4f);
+    p = __fadd_rn(__fmul_rn(p, z), 0x1.24924ap-3f);
+    p = __fadd_rn(__fmul_rn(p, z), 0x1.99999ap-3f);
+    p = __fadd_rn(__fmul_rn(p, z), 0x1.555556p-2f);
+    p = __fadd_rn(__fmul_rn(p, z), 1.0f);
+    const float lnm = __fmul_rn(__fadd_rn(s, s), p);
+    const float fe = __int2float_rn(e);
+    const float lo = __fadd_rn(__fmul_rn(fe, PG_LN2_LO), lnm);
+    return __fadd_rn(__fmul_rn(fe, PG_LN2_HI), lo);
+}
+
+__device__ __forceinline__ float f_exp(float y) {
+    const float t = __fadd_rn(__fmul_rn(y, PG_INV_LN2), 0.5f);
+    const int n = __float2int_rd(t);
+    const float fn = __int2float_rn(n);
+    float r = __fsub_rn(y, __fmul_rn(fn, PG_LN2_HI));
+    r = __fsub_rn(r, __fmul_rn(fn, PG_LN2_LO));
+    float p = 0x1.a01a02p-13f;
+    p = __fadd_rn(__fmul_rn(p, r), 0x1.6c16c2p-10f);
+    p = __fadd_rn(__fmul_rn(p, r), 0x1.111112p-7f);
+    p = __fadd_rn(__fmul_rn(p, r), 0x1.555556p-5f);
+    p = __fadd_rn(__fmul_rn(p, r), 0x1.555556p-3f);
+    p = __fadd_rn(__fmul_rn(p, r), 0.5f);
+    p = __fadd_rn(__fmul_rn(p, r), 1.0f);
+    p = __fadd_rn(__fmul_rn(p, r), 1.0f);
+    return __fmul_rn(p, __uint_as_float((uint32_t)(n + 127) << 23));
+}
+
+// (e^t - 1) / t
+__device__ __forceinline__ float f_phi(float t) {
+    if (fabsf(t) < 0.5f) {
+        float p = 0x1.71de3ap-19f;
+        p = __fadd_rn(__fmul_rn(p, t), 0x1.a01a02p-16f);
+        p = __fadd_rn(__fmul_rn(p, t), 0x1.a01a02p-13f);
+        p = __fadd_rn(__fmul_rn(p, t), 0x1.6c16c2p-10f);
+        p = __fadd_rn(__fmul_rn(p, t), 0x1.111112p-7f);
+        p = __fadd_rn(__fmul_rn(p, t), 0x1.555556p-5f);
+        p = __fadd_rn(__fmul_rn(p, t), 0x1.555556p-3f);
+        p = __fadd_rn(__fmul_rn(p, t), 0.5f);
+        p = __fadd_rn(__fmul_rn(p, t), 1.0f);
+        return p;
+    }
+    return __fdiv_rn(__fsub_rn(f_exp(t), 1.0f), t);
+}
+
+// ln(1 + t) / t
+__device__ __forceinline__ float f_psi(float t) {
+    if (fabsf(t) < 0.25f) {
+        float p = -0x1.555556p-4f;
+        p = __fadd_rn(__fmul_rn(p, t), 0x1.745d18p-4f);
+        p = __fadd_rn(__fmul_rn(p, t), -0x1.99999ap-4f);
+        p = __fadd_rn(__fmul_rn(p, t), 0x1.c71c72p-4f);
+        p = __fadd_rn(__fmul_rn(p, t), -0.125f);
+        p = __fadd_rn(__fmul_rn(p, t), 0x1.24924ap-3f);
+        p = __fadd_rn(__fmul_rn(p, t), -0x1.555556p-3f);
+        p = __fadd_rn(__fmul_rn(p, t), 0x1.99999ap-3f);
+        p = __fadd_rn(__fmul_rn(p, t), -0.25f);
+        p = __fadd_rn(__fmul_rn(p, t), 0x1.555556p-2f);
+        p = __fadd_rn(__fmul_rn(p, t), -0.5f);
+        p = __fadd_rn(__fmul_rn(p, t), 1.0f);
+        return p;
+    }
+    return __fdiv_rn(f_ln(__fadd_rn(1.0f, t)), t);
+}
+
+// ---------------------------------------------------------------- Zipf
+// Rejection-inversion (Hoermann and Derflinger, ACM TOMACS 1996) for
+// P(k) ~ k^-theta on [1, N]. h(x) = x^-theta, H(x) = int_1^x h,
+// H(x) = ln x * phi((1 - theta) ln x), H^-1(y) = exp(y * psi((1 - theta) y)).
+
+__device__ __forceinline__ float zipf_H(float x, float omt) {
+    const float L = f_ln(x);
+    return __fmul_rn(L, f_phi(__fmul_rn(omt, L)));
+}
+__device__ __forceinline__ float zipf_Hinv(float y, float omt) {
+    const float q = f_psi(__fmul_rn(omt, y));
+    return f_exp(__fmul_rn(y, q));
+}
+__device__ __forceinline__ float zipf_h(float x, float theta) {
+    return f_exp(-__fmul_rn(theta, f_ln(x)));
+}
+
+// Per-theta constants: A = H(3/2) - h(1), s = 2 - H^-1(H(5/2) - h(2)).
+__device__ __forceinline__ void zipf_theta_consts(float theta, float& omt, float& A, float& s) {
+    omt = __fsub_rn(1.0f, theta);
+    A = __fsub_rn(zipf_H(1.5f, omt), 1.0f);
+    const float h2 = __fsub_rn(zipf_H(2.5f, omt), zipf_h(2.0f, theta));
+    s = __fsub_rn(2.0f, zipf_Hinv(h2, omt));
+}
+// Per-support constant B = H(N + 1/2).
+__device__ __forceinline__ float zipf_B(uint64_t N, float omt) {
+    return zipf_H(__fadd_rn(__ull2float_rn(N), 0.5f), omt);
+}
+
+struct ZipfConsts {
+    float theta, omt, A, s;
+};
+
+// One trial with the 32-bit word w. Draws with k >= 256 are accepted without
+// the rejection test: there the exact rejection chance is below
+// theta (theta + 1) / (24 * 256^2) of h(k), smaller than binary32 rounding of H.
+__device__ __forceinline__ bool zipf_trial(const ZipfConsts& z, float B, uint64_t N, uint32_t w,
+                                           uint64_t& k_out) {
+    const float U = __fmul_rn(__uint2float_rn(w >> 8), 0x1p-24f);
+    const float u = __fadd_rn(B, __fmul_rn(U, __fsub_rn(z.A, B)));
+    const float x = zipf_Hinv(u, z.omt);
+    const float kf = floorf(__fadd_rn(x, 0.5f));
+    uint64_t k = kf < 1.0f ? 1ull : (uint64_t)__float2ull_rz(kf);
+    if (k > N) k = N;
+    k_out = k;
+    if (k >= 256u) return true;
+    const float fk = __ull2float_rn(k);
+    if (__fsub_rn(fk, x) <= z.s) return true;
+    const float Hk = __fsub_rn(zipf_H(__fadd_rn(fk, 0.5f), z.omt), zipf_h(fk, z.theta));
+    return u >= Hk;
+}
+
+// ---------------------------------------------------------------- the pair draw
+
+struct SamplerArgs {
+    const uint64_t* steps;     // packed step records [S]
+    const uint64_t* path_off;  // [P + 1]
+    const float* zipf_B;       // [P] H(n_p - 1/2); unused for n_p < 2
+    uint64_t n_steps;          // S
+    uint32_t n_paths;          // P
+    uint32_t T;                // iterations in the schedule
+    uint32_t t;                // this iteration
+    uint32_t key0, key1;       // Philox key = seed
+    ZipfConsts zc;
+};
+
+// Path table staged in shared memory by every block: offsets then Zipf B.
+struct PathTable {
+    const uint64_t* off;  // [P + 1]
+    const float* B;       // [P]
+    uint32_t P;
+};
+
+__device__ __forceinline__ uint32_t find_path(const uint64_t* off, uint32_t P, uint64_t g) {
+    uint32_t lo = 0, hi = P;  // off[lo] <= g < off[hi]
+    while (hi - lo > 1) {
+        const uint32_t mid = lo + ((hi - lo) >> 1);
+        if (off[mid] <= g) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+struct Pair {
+    uint64_t base;     // global index of the path's first step
+    uint64_t i, j;     // step indices within the path
+    uint64_t g;        // global step drawn
+    uint32_t path;
+    uint32_t w2;       // coin word: bit0 cooling coin, bit1 direction, bits 2-3 endpoints
+    uint32_t cooling;  // 1 = power-law pair
+    uint32_t short_path;  // 1 = path has < 2 steps: no update
+};
+
+// Draw the pair of update u in iteration t (Algorithm 1, lines 5-11).
+__device__ __forceinline__ Pair draw_pair(const SamplerArgs& a, const PathTable& pt, uint64_t u) {
+    Pair r;
+    const uint32_t c0 = (uint32_t)u, c1 = (uint32_t)(u >> 32);
+    const uint4 w = philox4x32_10(make_uint4(c0, c1, a.t, 0u), a.key0, a.key1);
+    const uint4 v = philox4x32_10(make_uint4(c0, c1, a.t, 1u), a.key0, a.key1);
+    r.g = mulhi64((uint64_t)w.x | ((uint64_t)w.y << 32), a.n_steps);
+    r.path = find_path(pt.off, pt.P, r.g);
+    r.base = pt.off[r.path];
+    const uint64_t n = pt.off[r.path + 1] - r.base;
+    r.i = r.g - r.base;
+    r.w2 = w.z;
+    r.cooling = (2ull * a.t >= a.T) || (w.z & 1u);
+    r.short_path = n < 2;
+    if (r.short_path) { r.j = r.i; return r; }
+    uint64_t j;
+    if (r.cooling) {
+        const float B = pt.B[r.path];
+        const uint64_t N = n - 1;
+        uint64_t k = 1;
+        bool ok = zipf_trial(a.zc, B, N, v.x, k) || zipf_trial(a.zc, B, N, v.y, k) ||
+                  zipf_trial(a.zc, B, N, v.z, k) || zipf_trial(a.zc, B, N, v.w, k);
+        for (uint32_t blk = 2; !ok && blk < 17; ++blk) {  // trials 4..63
+            const uint4 x = philox4x32_10(make_uint4(c0, c1, a.t, blk), a.key0, a.key1);
+            ok = zipf_trial(a.zc, B, N, x.x, k) || zipf_trial(a.zc, B, N, x.y, k) ||
+                 zipf_trial(a.zc, B, N, x.z, k) || zipf_trial(a.zc, B, N, x.w, k);
+        }
+        if (!ok) k = 1;
+        const uint64_t i = r.i;
+        const bool fwd = (w.z >> 1) & 1u;
+        const bool can_fwd = i + k < n, can_bwd = i >= k;
+        if (fwd && can_fwd) j = i + k;
+        else if (!fwd && can_bwd) j = i - k;
+        else if (can_fwd) j = i + k;
+        else if (can_bwd) j = i - k;
+        else j = (n - 1 - i > i) ? n - 1 : 0;
+    } else {
+        const uint64_t x = mulhi64((uint64_t)v.x | ((uint64_t)v.y << 32), n - 1);
+        j = x + (x >= r.i);
+    }
+    r.j = j;
+    return r;
+}
+
+}  // namespace pgsgd

@@ -1,0 +1,608 @@
+// CUDA kernels of the PG-SGD path for GB300 (sm_103a): graph ingest and
+// validation, the lock-free update kernel of Algorithm 1, the sampled
+// path-stress kernel of Eq. 2, coordinate conversion and the debug kernels
+// that expose the sampler and a Jacobi sweep for parity checks.
+//
+// The path is a random gather/scatter over HBM (Section III-B: memory bound,
+// no dense contraction), so there are no tensor cores here: the design goal is
+// bytes per update. Each update reads two 8-byte step records and two 32-byte
+// node records (one DRAM sector each) and writes back 8 bytes of each node.
+#include <cstdio>
+
+#include "../../include/pgsgd.h"
+#include "pgsgd_internal.h"
+
+namespace pgsgd {
+
+namespace {
+
+__device__ __forceinline__ uint32_t find_off(const uint64_t* off, uint32_t P, uint64_t g) {
+    return find_path(off, P, g);
+}
+
+// ---------------------------------------------------------------- ingest
+
+__global__ void pack_nodes_kernel(const uint32_t* __restrict__ node_len, uint32_t n,
+                                  NodeRec* __restrict__ nodes, uint32_t* flags) {
+    uint32_t bad = 0;
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
+         v += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t len = node_len[v];
+        if (len == 0) bad |= FLAG_ZERO_LEN;
+        NodeRec r;
+        r.sx = r.sy = r.ex = r.ey = 0.0f;
+        r.ax = r.ay = 0;
+        r.len = len;
+        r.pad = 0;
+        nodes[v] = r;
+    }
+    if (bad) atomicOr(flags, bad);
+}
+
+__global__ void pack_steps_kernel(const uint32_t* __restrict__ step_node,
+                                  const uint8_t* __restrict__ step_rev,
+                                  const int64_t* __restrict__ step_pos,
+                                  const uint32_t* __restrict__ node_len, uint32_t n_nodes,
+                                  const uint64_t* __restrict__ path_off, uint32_t P, uint64_t S,
+                                  uint64_t* __restrict__ steps, uint32_t* flags) {
+    extern __shared__ uint64_t s_off[];
+    for (uint32_t k = threadIdx.x; k <= P; k += blockDim.x) s_off[k] = path_off[k];
+    __syncthreads();
+    uint32_t bad = 0;
+    for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < S;
+         s += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t p = find_off(s_off, P, s);
+        const bool first = s == s_off[p];
+        const bool last = s + 1 == s_off[p + 1];
+        const uint32_t nd = step_node[s];
+        const uint32_t rv = step_rev[s];
+        const int64_t ps = step_pos[s];
+        if (nd >= n_nodes) bad |= FLAG_BAD_NODE;
+        if (rv > 1) bad |= FLAG_BAD_REV;
+        if (ps < 0 || ps >= (int64_t)(1ll << 32)) bad |= FLAG_POS_RANGE;
+        if (first && ps != 0) bad |= FLAG_BAD_POS;
+        if (!last && nd < n_nodes && step_pos[s + 1] != ps + (int64_t)node_len[nd])
+            bad |= FLAG_BAD_POS;
+        steps[s] = pack_step(nd & 0x7fffffffu, rv, (uint64_t)ps & 0xffffffffull);
+    }
+    if (bad) atomicOr(flags, bad);
+}
+
+__global__ void path_extent_kernel(const uint64_t* __restrict__ steps,
+                                   const uint64_t* __restrict__ path_off,
+                                   const NodeRec* __restrict__ nodes, uint32_t P,
+                                   int64_t* __restrict__ out_nt) {
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const uint64_t a = path_off[p], b = path_off[p + 1];
+    if (a == b) { out_nt[p] = 0; return; }
+    const uint64_t s = steps[b - 1];
+    out_nt[p] = step_pos(s) + (int64_t)nodes[step_node(s)].len;
+}
+
+// ---------------------------------------------------------------- coordinates
+
+__global__ void set_coords_kernel(const double* __restrict__ xy, NodeRec* __restrict__ nodes,
+                                  uint32_t n, int anchored, uint32_t* flags) {
+    uint32_t bad = 0;
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
+         v += (uint64_t)gridDim.x * blockDim.x) {
+        const double sx = xy[4 * v], sy = xy[4 * v + 1], ex = xy[4 * v + 2], ey = xy[4 * v + 3];
+        if (!isfinite(sx) || !isfinite(sy) || !isfinite(ex) || !isfinite(ey)) bad |= FLAG_COORD_NAN;
+        NodeRec r = nodes[v];
+        int32_t ax = 0, ay = 0;
+        if (anchored) {
+            const double lim = 1073741824.0;  // 2^30
+            if (fabs(sx) >= lim || fabs(sy) >= lim || fabs(ex) >= lim || fabs(ey) >= lim)
+                bad |= FLAG_COORD_RANGE;
+            else {
+                ax = (int32_t)rint(sx);
+                ay = (int32_t)rint(sy);
+            }
+        }
+        r.ax = ax;
+        r.ay = ay;
+        r.sx = (float)(sx - ax);
+        r.sy = (float)(sy - ay);
+        r.ex = (float)(ex - ax);
+        r.ey = (float)(ey - ay);
+        nodes[v] = r;
+    }
+    if (bad) atomicOr(flags, bad);
+}
+
+__global__ void get_coords_kernel(const NodeRec* __restrict__ nodes, double* __restrict__ xy,
+                                  uint32_t n) {
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
+         v += (uint64_t)gridDim.x * blockDim.x) {
+        const NodeRec r = nodes[v];
+        xy[4 * v] = (double)r.ax + (double)r.sx;
+        xy[4 * v + 1] = (double)r.ay + (double)r.sy;
+        xy[4 * v + 2] = (double)r.ax + (double)r.ex;
+        xy[4 * v + 3] = (double)r.ay + (double)r.ey;
+    }
+}
+
+// Move each anchor to the rounded start point so offsets stay near zero.
+// Subtracting an integer within half a unit of sx leaves sx exact.
+__global__ void rebase_kernel(NodeRec* __restrict__ nodes, uint32_t n) {
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
+         v += (uint64_t)gridDim.x * blockDim.x) {
+        NodeRec r = nodes[v];
+        bool changed = false;
+        if (fabsf(r.sx) > 8.0f) {
+            const float sh = rintf(r.sx);
+            const int64_t na = (int64_t)r.ax + (int64_t)sh;
+            if (na > -(1ll << 30) && na < (1ll << 30)) {
+                r.ax = (int32_t)na; r.sx -= sh; r.ex -= sh; changed = true;
+            }
+        }
+        if (fabsf(r.sy) > 8.0f) {
+            const float sh = rintf(r.sy);
+            const int64_t na = (int64_t)r.ay + (int64_t)sh;
+            if (na > -(1ll << 30) && na < (1ll << 30)) {
+                r.ay = (int32_t)na; r.sy -= sh; r.ey -= sh; changed = true;
+            }
+        }
+        if (changed) nodes[v] = r;
+    }
+}
+
+// ---------------------------------------------------------------- Zipf per path
+
+__global__ void zipf_setup_kernel(const uint64_t* __restrict__ path_off, uint32_t P, float theta,
+                                  float* __restrict__ out_B) {
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const uint64_t n = path_off[p + 1] - path_off[p];
+    const float omt = __fsub_rn(1.0f, theta);
+    out_B[p] = n >= 2 ? zipf_B(n - 1, omt) : 0.0f;
+}
+
+// Stage the path table and the per-theta Zipf constants in shared memory.
+__device__ __forceinline__ PathTable stage_paths(const SamplerArgs& a, unsigned char* smem,
+                                                 ZipfConsts& zc_shared) {
+    uint64_t* s_off = reinterpret_cast<uint64_t*>(smem);
+    float* s_B = reinterpret_cast<float*>(s_off + a.n_paths + 1);
+    for (uint32_t k = threadIdx.x; k <= a.n_paths; k += blockDim.x) s_off[k] = a.path_off[k];
+    for (uint32_t k = threadIdx.x; k < a.n_paths; k += blockDim.x) s_B[k] = a.zipf_B[k];
+    if (threadIdx.x == 0) {
+        ZipfConsts z;
+        z.theta = a.zc.theta;
+        zipf_theta_consts(z.theta, z.omt, z.A, z.s);
+        zc_shared = z;
+    }
+    __syncthreads();
+    return PathTable{s_off, s_B, a.n_paths};
+}
+
+// ---------------------------------------------------------------- update math
+
+struct Move {
+    float dxi, dyi, dxj, dyj;  // change of v_i and v_j
+    bool moved;
+};
+
+// The update of Zheng et al. that Algorithm 1, line 15 applies (Fig. 3):
+// w = d^-2, mu = min(eta w, 1), r = mu (|v_i - v_j| - d) / (2 |v_i - v_j|),
+// v_i -= r (v_i - v_j), v_j += r (v_i - v_j). FP32, anchors differenced in
+// integers so chromosome-scale coordinates keep their resolution.
+__device__ __forceinline__ Move pair_move(const NodeRec& a, uint32_t ea, const NodeRec& b,
+                                          uint32_t eb, int64_t d, float eta) {
+    Move m;
+    const float xa = ea ? a.ex : a.sx, ya = ea ? a.ey : a.sy;
+    const float xb = eb ? b.ex : b.sx, yb = eb ? b.ey : b.sy;
+    const float dx = __ll2float_rn((int64_t)a.ax - (int64_t)b.ax) + (xa - xb);
+    const float dy = __ll2float_rn((int64_t)a.ay - (int64_t)b.ay) + (ya - yb);
+    const float mag = sqrtf(dx * dx + dy * dy);
+    m.moved = mag > 0.0f;
+    const float df = __ll2float_rn(d);
+    const float w = 1.0f / (df * df);
+    const float mu = fminf(eta * w, 1.0f);
+    const float r = m.moved ? mu * (mag - df) / (2.0f * mag) : 0.0f;
+    const float rx = r * dx, ry = r * dy;
+    m.dxi = -rx; m.dyi = -ry; m.dxj = rx; m.dyj = ry;
+    return m;
+}
+
+// ---------------------------------------------------------------- the update kernel
+
+// One launch = one iteration's N updates (or a slice), grid-stride over the
+// update index u. Every thread keeps UPT independent updates in flight per
+// loop trip: all draws first (ALU), then all step-record loads, then all
+// node-record loads, then the moves, so that 2 * UPT DRAM requests per
+// thread overlap instead of queueing behind each other.
+template <int UPT, bool ATOMIC>
+__global__ void update_kernel(UpdateLaunch L) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ ZipfConsts zc;
+    const PathTable pt = stage_paths(L.s, smem, zc);
+    SamplerArgs a = L.s;
+    a.zc = zc;
+    const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t gtid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint64_t* __restrict__ steps = a.steps;
+    NodeRec* __restrict__ nodes = L.nodes;
+    for (uint64_t base = gtid; base < L.n_updates; base += nthr * UPT) {
+        Pair pr[UPT];
+        bool act[UPT];
+#pragma unroll
+        for (int k = 0; k < UPT; ++k) {
+            const uint64_t u = base + (uint64_t)k * nthr;
+            act[k] = u < L.n_updates;
+            if (act[k]) {
+                pr[k] = draw_pair(a, pt, L.u_begin + u);
+                act[k] = !pr[k].short_path;
+            }
+        }
+        uint64_t si[UPT], sj[UPT];
+#pragma unroll
+        for (int k = 0; k < UPT; ++k) {
+            if (act[k]) {
+                si[k] = load_step(steps + pr[k].base + pr[k].i);
+                sj[k] = load_step(steps + pr[k].base + pr[k].j);
+            }
+        }
+        NodeRec na[UPT], nb[UPT];
+#pragma unroll
+        for (int k = 0; k < UPT; ++k) {
+            if (act[k]) {
+                na[k] = load_node(nodes + step_node(si[k]));
+                nb[k] = load_node(nodes + step_node(sj[k]));
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < UPT; ++k) {
+            if (!act[k]) continue;
+            const uint32_t ea = (pr[k].w2 >> 2) & 1u, eb = (pr[k].w2 >> 3) & 1u;
+            const int64_t pa = endpoint_pos(si[k], ea, na[k].len);
+            const int64_t pb = endpoint_pos(sj[k], eb, nb[k].len);
+            const int64_t d = pa > pb ? pa - pb : pb - pa;
+            if (d == 0) continue;
+            const Move m = pair_move(na[k], ea, nb[k], eb, d, L.eta);
+            if (!m.moved) continue;
+            float* pa_ptr = &nodes[step_node(si[k])].sx + 2 * ea;
+            float* pb_ptr = &nodes[step_node(sj[k])].sx + 2 * eb;
+            if (ATOMIC) {
+                atomicAdd(reinterpret_cast<float2*>(pa_ptr), make_float2(m.dxi, m.dyi));
+                atomicAdd(reinterpret_cast<float2*>(pb_ptr), make_float2(m.dxj, m.dyj));
+            } else {
+                const float xa = ea ? na[k].ex : na[k].sx, ya = ea ? na[k].ey : na[k].sy;
+                const float xb = eb ? nb[k].ex : nb[k].sx, yb = eb ? nb[k].ey : nb[k].sy;
+                *reinterpret_cast<float2*>(pa_ptr) = make_float2(xa + m.dxi, ya + m.dyi);
+                *reinterpret_cast<float2*>(pb_ptr) = make_float2(xb + m.dxj, yb + m.dyj);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- debug kernels
+
+__global__ void debug_sample_kernel(SamplerArgs a0, uint64_t u_begin, uint64_t count,
+                                    const NodeRec* __restrict__ nodes, pgsgd_sample* out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ ZipfConsts zc;
+    const PathTable pt = stage_paths(a0, smem, zc);
+    SamplerArgs a = a0;
+    a.zc = zc;
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < count;
+         q += (uint64_t)gridDim.x * blockDim.x) {
+        const Pair pr = draw_pair(a, pt, u_begin + q);
+        pgsgd_sample r;
+        r.g = pr.g; r.i = pr.i; r.j = pr.j; r.path = pr.path;
+        r.cooling = (uint8_t)pr.cooling;
+        r.e_i = (pr.w2 >> 2) & 1u;
+        r.e_j = (pr.w2 >> 3) & 1u;
+        r.d_ref = 0;
+        if (pr.short_path) {
+            r.skip = 1;
+        } else {
+            const uint64_t si = load_step(a.steps + pr.base + pr.i);
+            const uint64_t sj = load_step(a.steps + pr.base + pr.j);
+            const int64_t pa = endpoint_pos(si, r.e_i, nodes[step_node(si)].len);
+            const int64_t pb = endpoint_pos(sj, r.e_j, nodes[step_node(sj)].len);
+            r.d_ref = pa > pb ? pa - pb : pb - pa;
+            r.skip = r.d_ref == 0 ? 2 : 0;
+        }
+        out[q] = r;
+    }
+}
+
+__global__ void debug_sweep_kernel(SamplerArgs a0, uint64_t u_begin, uint64_t count,
+                                   const NodeRec* __restrict__ nodes, float eta, float4* out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ ZipfConsts zc;
+    const PathTable pt = stage_paths(a0, smem, zc);
+    SamplerArgs a = a0;
+    a.zc = zc;
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < count;
+         q += (uint64_t)gridDim.x * blockDim.x) {
+        const Pair pr = draw_pair(a, pt, u_begin + q);
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!pr.short_path) {
+            const uint64_t si = load_step(a.steps + pr.base + pr.i);
+            const uint64_t sj = load_step(a.steps + pr.base + pr.j);
+            const NodeRec na = load_node(nodes + step_node(si));
+            const NodeRec nb = load_node(nodes + step_node(sj));
+            const uint32_t ea = (pr.w2 >> 2) & 1u, eb = (pr.w2 >> 3) & 1u;
+            const int64_t pa = endpoint_pos(si, ea, na.len), pb = endpoint_pos(sj, eb, nb.len);
+            const int64_t d = pa > pb ? pa - pb : pb - pa;
+            if (d != 0) {
+                const Move m = pair_move(na, ea, nb, eb, d, eta);
+                if (m.moved) o = make_float4(m.dxi, m.dyi, m.dxj, m.dyj);
+            }
+        }
+        out[q] = o;
+    }
+}
+
+// ---------------------------------------------------------------- sampled stress
+
+template <int SPT>
+__global__ void stress_kernel(StressLaunch L) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t* s_soff = reinterpret_cast<uint64_t*>(smem);   // [P + 1] sample offsets
+    uint64_t* s_poff = s_soff + L.n_paths + 1;              // [P + 1] step offsets
+    for (uint32_t k = threadIdx.x; k <= L.n_paths; k += blockDim.x) {
+        s_soff[k] = L.sample_off[k];
+        s_poff[k] = L.path_off[k];
+    }
+    __syncthreads();
+    const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t gtid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    double sum = 0.0, sq = 0.0, cnt = 0.0;
+    // running per-path sums, flushed to global when the path changes
+    uint32_t cur_p = 0xffffffffu;
+    double ps = 0.0, pq = 0.0, pc = 0.0;
+    for (uint64_t base = gtid; base < L.n_samples; base += nthr * SPT) {
+        uint32_t p[SPT];
+        uint64_t si[SPT], sj[SPT];
+        uint32_t ei[SPT], ej[SPT];
+        bool act[SPT];
+#pragma unroll
+        for (int k = 0; k < SPT; ++k) {
+            const uint64_t Q = base + (uint64_t)k * nthr;
+            act[k] = Q < L.n_samples;
+            if (!act[k]) continue;
+            p[k] = find_path(s_soff, L.n_paths, Q);
+            const uint64_t q = Q - s_soff[p[k]];
+            const uint64_t off = s_poff[p[k]];
+            const uint64_t n = s_poff[p[k] + 1] - off;
+            const uint32_t c2 = 0x80000000u | p[k];
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), c2, 0u),
+                                          L.key0, L.key1);
+            const uint4 v = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), c2, 1u),
+                                          L.key0, L.key1);
+            const uint64_t i = mulhi64((uint64_t)w.x | ((uint64_t)w.y << 32), n);
+            const uint64_t x = mulhi64((uint64_t)v.x | ((uint64_t)v.y << 32), n - 1);
+            const uint64_t j = x + (x >= i);
+            ei[k] = w.z & 1u;
+            ej[k] = (w.z >> 1) & 1u;
+            si[k] = load_step(L.steps + off + i);
+            sj[k] = load_step(L.steps + off + j);
+        }
+        NodeRec na[SPT], nb[SPT];
+#pragma unroll
+        for (int k = 0; k < SPT; ++k) {
+            if (!act[k]) continue;
+            na[k] = load_node(L.nodes + step_node(si[k]));
+            nb[k] = load_node(L.nodes + step_node(sj[k]));
+        }
+#pragma unroll
+        for (int k = 0; k < SPT; ++k) {
+            if (!act[k]) continue;
+            const int64_t pa = endpoint_pos(si[k], ei[k], na[k].len);
+            const int64_t pb = endpoint_pos(sj[k], ej[k], nb[k].len);
+            const int64_t d = pa > pb ? pa - pb : pb - pa;
+            if (d == 0) continue;
+            const float xa = ei[k] ? na[k].ex : na[k].sx, ya = ei[k] ? na[k].ey : na[k].sy;
+            const float xb = ej[k] ? nb[k].ex : nb[k].sx, yb = ej[k] ? nb[k].ey : nb[k].sy;
+            const float dx = __ll2float_rn((int64_t)na[k].ax - (int64_t)nb[k].ax) + (xa - xb);
+            const float dy = __ll2float_rn((int64_t)na[k].ay - (int64_t)nb[k].ay) + (ya - yb);
+            const float df = __ll2float_rn(d);
+            const float t = (sqrtf(dx * dx + dy * dy) - df) / df;
+            const float term = t * t;
+            sum += (double)term;
+            sq += (double)term * (double)term;
+            cnt += 1.0;
+            if (L.per_path) {
+                if (p[k] != cur_p) {
+                    if (cur_p != 0xffffffffu) {
+                        atomicAdd(L.per_path + 3 * (uint64_t)cur_p, ps);
+                        atomicAdd(L.per_path + 3 * (uint64_t)cur_p + 1, pq);
+                        atomicAdd(L.per_path + 3 * (uint64_t)cur_p + 2, pc);
+                    }
+                    cur_p = p[k]; ps = pq = pc = 0.0;
+                }
+                ps += (double)term; pq += (double)term * (double)term; pc += 1.0;
+            }
+        }
+    }
+    if (L.per_path && cur_p != 0xffffffffu) {
+        atomicAdd(L.per_path + 3 * (uint64_t)cur_p, ps);
+        atomicAdd(L.per_path + 3 * (uint64_t)cur_p + 1, pq);
+        atomicAdd(L.per_path + 3 * (uint64_t)cur_p + 2, pc);
+    }
+    // block reduction in a fixed order: warp shuffles, then warp 0
+    __shared__ double red[3][32];
+    for (int off = 16; off > 0; off >>= 1) {
+        sum += __shfl_down_sync(0xffffffffu, sum, off);
+        sq += __shfl_down_sync(0xffffffffu, sq, off);
+        cnt += __shfl_down_sync(0xffffffffu, cnt, off);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { red[0][warp] = sum; red[1][warp] = sq; red[2][warp] = cnt; }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        sum = lane < nw ? red[0][lane] : 0.0;
+        sq = lane < nw ? red[1][lane] : 0.0;
+        cnt = lane < nw ? red[2][lane] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) {
+            sum += __shfl_down_sync(0xffffffffu, sum, off);
+            sq += __shfl_down_sync(0xffffffffu, sq, off);
+            cnt += __shfl_down_sync(0xffffffffu, cnt, off);
+        }
+        if (lane == 0) {
+            L.partials[3 * (uint64_t)blockIdx.x] = sum;
+            L.partials[3 * (uint64_t)blockIdx.x + 1] = sq;
+            L.partials[3 * (uint64_t)blockIdx.x + 2] = cnt;
+        }
+    }
+}
+
+// Sum the per-block partials in a fixed order (one block of 256 threads).
+__global__ void stress_finalize_kernel(const double* __restrict__ partials, int n,
+                                       double* __restrict__ out3) {
+    __shared__ double red[3][256];
+    double s = 0.0, q = 0.0, c = 0.0;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) {
+        s += partials[3 * b];
+        q += partials[3 * b + 1];
+        c += partials[3 * b + 2];
+    }
+    red[0][threadIdx.x] = s; red[1][threadIdx.x] = q; red[2][threadIdx.x] = c;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + w];
+            red[1][threadIdx.x] += red[1][threadIdx.x + w];
+            red[2][threadIdx.x] += red[2][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { out3[0] = red[0][0]; out3[1] = red[1][0]; out3[2] = red[2][0]; }
+}
+
+int grid_for(uint64_t work, int block, int sm_count, int per_sm) {
+    uint64_t g = (work + block - 1) / block;
+    const uint64_t cap = (uint64_t)sm_count * per_sm;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+}  // namespace
+
+size_t update_smem_bytes(uint32_t n_paths) {
+    return (size_t)(n_paths + 1) * sizeof(uint64_t) + (size_t)n_paths * sizeof(float);
+}
+size_t stress_smem_bytes(uint32_t n_paths) { return 2 * (size_t)(n_paths + 1) * sizeof(uint64_t); }
+
+cudaError_t launch_pack_nodes(const uint32_t* node_len, uint32_t n, NodeRec* nodes,
+                              uint32_t* flags, int sm_count, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    pack_nodes_kernel<<<grid_for(n, 256, sm_count, 16), 256, 0, st>>>(node_len, n, nodes, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_steps(const uint32_t* step_node, const uint8_t* step_rev,
+                              const int64_t* step_pos, const uint32_t* node_len, uint32_t n_nodes,
+                              const uint64_t* path_off, uint32_t n_paths, uint64_t n_steps,
+                              uint64_t* steps, uint32_t* flags, int sm_count, cudaStream_t st) {
+    if (n_steps == 0) return cudaSuccess;
+    const size_t smem = (size_t)(n_paths + 1) * sizeof(uint64_t);
+    cudaError_t e = cudaFuncSetAttribute(pack_steps_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    pack_steps_kernel<<<grid_for(n_steps, 256, sm_count, 8), 256, smem, st>>>(
+        step_node, step_rev, step_pos, node_len, n_nodes, path_off, n_paths, n_steps, steps, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_path_extent(const uint64_t* steps, const uint64_t* path_off, const NodeRec* nodes,
+                               uint32_t n_paths, int64_t* out_nt, cudaStream_t st) {
+    path_extent_kernel<<<(n_paths + 127) / 128, 128, 0, st>>>(steps, path_off, nodes, n_paths, out_nt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_coords(const double* xy, NodeRec* nodes, uint32_t n, int anchored,
+                              uint32_t* flags, int sm_count, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    set_coords_kernel<<<grid_for(n, 256, sm_count, 16), 256, 0, st>>>(xy, nodes, n, anchored, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_get_coords(const NodeRec* nodes, double* xy, uint32_t n, int sm_count,
+                              cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    get_coords_kernel<<<grid_for(n, 256, sm_count, 16), 256, 0, st>>>(nodes, xy, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rebase(NodeRec* nodes, uint32_t n, int sm_count, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    rebase_kernel<<<grid_for(n, 256, sm_count, 16), 256, 0, st>>>(nodes, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zipf_setup(const uint64_t* path_off, uint32_t n_paths, float theta,
+                              float* zipf_B, float*, cudaStream_t st) {
+    if (n_paths == 0) return cudaSuccess;
+    zipf_setup_kernel<<<(n_paths + 127) / 128, 128, 0, st>>>(path_off, n_paths, theta, zipf_B);
+    return cudaGetLastError();
+}
+
+template <int UPT, bool ATOMIC>
+static cudaError_t launch_update_t(const UpdateLaunch& L, cudaStream_t st) {
+    const size_t smem = update_smem_bytes(L.s.n_paths);
+    cudaError_t e = cudaFuncSetAttribute(update_kernel<UPT, ATOMIC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    update_kernel<UPT, ATOMIC><<<L.grid, L.block, smem, st>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update(const UpdateLaunch& L, cudaStream_t st) {
+    if (L.n_updates == 0) return cudaSuccess;
+    switch (L.upt * 2 + (L.atomic ? 1 : 0)) {
+        case 2: return launch_update_t<1, false>(L, st);
+        case 3: return launch_update_t<1, true>(L, st);
+        case 4: return launch_update_t<2, false>(L, st);
+        case 5: return launch_update_t<2, true>(L, st);
+        case 8: return launch_update_t<4, false>(L, st);
+        case 9: return launch_update_t<4, true>(L, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_debug_sample(const SamplerArgs& s, uint64_t u_begin, uint64_t count,
+                                const NodeRec* nodes, void* out, int sm_count, cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    const size_t smem = update_smem_bytes(s.n_paths);
+    cudaError_t e = cudaFuncSetAttribute(debug_sample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    debug_sample_kernel<<<grid_for(count, 256, sm_count, 8), 256, smem, st>>>(
+        s, u_begin, count, nodes, static_cast<pgsgd_sample*>(out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debug_sweep(const SamplerArgs& s, uint64_t u_begin, uint64_t count,
+                               const NodeRec* nodes, float eta, float4* out, int sm_count,
+                               cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    const size_t smem = update_smem_bytes(s.n_paths);
+    cudaError_t e = cudaFuncSetAttribute(debug_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    debug_sweep_kernel<<<grid_for(count, 256, sm_count, 8), 256, smem, st>>>(s, u_begin, count, nodes,
+                                                                             eta, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stress(const StressLaunch& L, cudaStream_t st) {
+    const size_t smem = stress_smem_bytes(L.n_paths);
+    cudaError_t e = cudaFuncSetAttribute(stress_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    stress_kernel<2><<<L.grid, L.block, smem, st>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stress_finalize(const double* partials, int n, double* out3, cudaStream_t st) {
+    stress_finalize_kernel<<<1, 256, 0, st>>>(partials, n, out3);
+    return cudaGetLastError();
+}
+
+}  // namespace pgsgd

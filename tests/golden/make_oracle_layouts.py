@@ -1,0 +1,72 @@
+"""Write tests/golden/oracle_layouts.json: the CPU oracle's layout quality.
+
+For each workload and layout seed this runs Algorithm 1 in the oracle (FP64,
+Hogwild! threads on the host's cores for the two larger graphs) from the
+generator's initial layout and records the sampled path stress (Eq. 2) of
+the result under a fixed stress seed. Only the oracle and the input
+generator are called. The GPU tests compare the CUDA layout's stress, under
+the same seeds, against these values.
+
+    python tests/golden/make_oracle_layouts.py [--configs mid chrom] [--threads 6]
+"""
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import oracle as O  # noqa: E402
+from synth import make_graph  # noqa: E402
+
+OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_layouts.json")
+PLAN = {
+    # name: (layout seeds, stress samples per step, stress seed)
+    "tiny": ([1, 2, 3, 4, 5], 100, 7),
+    "mid": ([1, 2], 100, 7),
+    "chrom": ([1], 10, 7),
+}
+
+
+def fingerprint(g):
+    return dict(n_nodes=g.n_nodes, n_paths=g.n_paths, n_steps=g.n_steps,
+                pos_sum=int(g.step_pos.sum() % (1 << 61)),
+                node_sum=int(g.step_node.astype(np.int64).sum()),
+                rev_sum=int(g.step_rev.sum()), len_sum=int(g.node_len.astype(np.int64).sum()))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--configs", nargs="+", default=list(PLAN))
+    ap.add_argument("--threads", type=int, default=os.cpu_count())
+    args = ap.parse_args()
+    data = json.load(open(OUT)) if os.path.exists(OUT) else {}
+    for name in args.configs:
+        seeds, per_step, sseed = PLAN[name]
+        g = make_graph(name)
+        threads = 1 if name == "tiny" else args.threads
+        entry = dict(fingerprint=fingerprint(g), iterations=30, theta=0.99, updates_per_step=10,
+                     stress_samples_per_step=per_step, stress_seed=sseed, oracle_threads=threads,
+                     runs=[])
+        init = O.sampled_stress(g, g.init_xy, per_step=per_step, seed=sseed, n_threads=args.threads)
+        entry["init_stress"] = init["mean"]
+        for seed in seeds:
+            t0 = time.time()
+            xy, moved = O.layout(g, g.init_xy, T=30, theta=0.99, seed=seed, n_threads=threads)
+            t1 = time.time()
+            st = O.sampled_stress(g, xy, per_step=per_step, seed=sseed, n_threads=args.threads)
+            entry["runs"].append(dict(seed=seed, stress=st["mean"], ci_lo=st["ci_lo"],
+                                      ci_hi=st["ci_hi"], n_valid=st["n_valid"], moved=moved,
+                                      layout_seconds=round(t1 - t0, 1)))
+            print(name, seed, st["mean"], round(t1 - t0, 1), "s", flush=True)
+            data[name] = entry
+            with open(OUT, "w") as f:
+                json.dump(data, f, indent=1)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,146 @@
+"""Hogwild! layouts on the GPU against the oracle's layouts (stress level).
+
+GPU and oracle apply the same draws in different orders (lock-free threads
+vs the oracle's loop), so their layouts differ; parity is judged on the
+sampled path stress (Eq. 2) of the results under the same stress seed. The
+oracle's numbers for the two larger graphs come from
+tests/golden/make_oracle_layouts.py.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from synth import make_graph, make_linear_path
+
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "oracle_layouts.json")
+T = 30
+
+
+@pytest.fixture(scope="module")
+def pg():
+    import paper_2409_00876_gb300 as pg
+    pg.load_library()
+    return pg
+
+
+def _gold(name):
+    if not os.path.exists(GOLD):
+        pytest.skip("no oracle layout record")
+    data = json.load(open(GOLD))
+    if name not in data or not data[name]["runs"]:
+        pytest.skip(f"no oracle layout record for {name}")
+    return data[name]
+
+
+def _layout_stress(pg, g, seed, per_step, sseed, **opts):
+    G = pg.Graph.from_synth(g)
+    for k, v in opts.items():
+        G.set_option(k, v)
+    G.set_coords(g.init_xy)
+    G.layout(T, theta=0.99, seed=seed)
+    return G.stress(per_step, seed=sseed), G
+
+
+def test_linear_path_converges_on_gpu(pg):
+    g = make_linear_path(3000, len_mean=8, seed=4, jitter=3.0)
+    st, _ = _layout_stress(pg, g, 3, 100, 2)
+    assert st["mean"] < 1e-3
+
+
+def test_tiny_layout_quality_matches_oracle(pg):
+    g = make_graph("tiny")
+    ref = []
+    got = []
+    for seed in range(1, 6):
+        xy, _ = O.layout(g, g.init_xy, T=T, theta=0.99, seed=seed)
+        ref.append(O.sampled_stress(g, xy, seed=7)["mean"])
+        got.append(_layout_stress(pg, g, seed, 100, 7)[0]["mean"])
+    ref, got = np.array(ref), np.array(got)
+    # the seed-to-seed spread of the oracle itself sets how close means can be
+    se = np.hypot(ref.std(ddof=1), got.std(ddof=1)) / np.sqrt(len(ref))
+    assert abs(got.mean() - ref.mean()) <= max(0.01 * ref.mean(), 3 * se), (got, ref)
+
+
+@pytest.mark.parametrize("name", ["mid", "chrom"])
+def test_layout_stress_within_one_percent_of_oracle(pg, name):
+    gold = _gold(name)
+    g = make_graph(name)
+    fp = gold["fingerprint"]
+    assert (g.n_nodes, g.n_paths, g.n_steps) == (fp["n_nodes"], fp["n_paths"], fp["n_steps"])
+    per, sseed = gold["stress_samples_per_step"], gold["stress_seed"]
+    for run in gold["runs"]:
+        st, G = _layout_stress(pg, g, run["seed"], per, sseed)
+        rel = abs(st["mean"] - run["stress"]) / run["stress"]
+        print(name, run["seed"], st["mean"], run["stress"], rel)
+        assert rel <= 0.01, (st["mean"], run["stress"])
+        assert st["mean"] < 0.5 * gold["init_stress"]
+
+
+def test_atomic_and_plain_updates_reach_same_quality(pg):
+    g = make_graph("mid")
+    a, _ = _layout_stress(pg, g, 1, 20, 7, atomic_updates=0)
+    b, _ = _layout_stress(pg, g, 1, 20, 7, atomic_updates=1)
+    assert abs(a["mean"] - b["mean"]) <= 0.05 * a["mean"]
+
+
+def test_resume_in_two_calls_matches_one_call_quality(pg):
+    g = make_graph("mid")
+    G = pg.Graph.from_synth(g)
+    G.set_coords(g.init_xy)
+    G.layout(T, theta=0.99, seed=5, iter_end=12)
+    G.layout(T, theta=0.99, seed=5, iter_begin=12)
+    two = G.stress(20, seed=7)["mean"]
+    one = _layout_stress(pg, g, 5, 20, 7)[0]["mean"]
+    assert abs(two - one) <= 0.05 * one
+
+
+def test_plain_fp32_coordinates_lose_resolution_at_chromosome_scale(pg):
+    # Anchored offsets keep sub-nucleotide resolution where plain FP32 cannot
+    # (ulp 16 at 1.7e8): the plain layout's stress is visibly worse.
+    g = make_graph("chrom", backbone=2_000_000, paths=8)
+    xy = g.init_xy.copy()
+    xy[:, [0, 2]] += 1.5e8  # move the graph far from the origin
+    res = {}
+    for mode in (0, 1):
+        G = pg.Graph.from_synth(g)
+        G.set_option("coord_mode", mode)
+        G.set_coords(xy)
+        G.layout(T, theta=0.99, seed=1)
+        res[mode] = G.stress(5, seed=7)["mean"]
+    assert res[1] > 2 * res[0], res
+
+
+def test_create_rejects_inconsistent_graphs(pg):
+    from paper_2409_00876_gb300 import PgsgdError
+    g = make_graph("tiny")
+    bad_node = g.step_node.copy()
+    bad_node[100] = g.n_nodes
+    with pytest.raises(PgsgdError, match="node id"):
+        pg.Graph(g.node_len, g.path_off, bad_node, g.step_rev, g.step_pos)
+    bad_pos = g.step_pos.copy()
+    bad_pos[200] += 1
+    with pytest.raises(PgsgdError, match="positions"):
+        pg.Graph(g.node_len, g.path_off, g.step_node, g.step_rev, bad_pos)
+    bad_rev = g.step_rev.copy()
+    bad_rev[5] = 2
+    with pytest.raises(PgsgdError, match="orientation"):
+        pg.Graph(g.node_len, g.path_off, g.step_node, bad_rev, g.step_pos)
+    zero = g.node_len.copy()
+    zero[0] = 0
+    with pytest.raises(PgsgdError):
+        pg.Graph(zero, g.path_off, g.step_node, g.step_rev, g.step_pos)
+    G = pg.Graph.from_synth(g)
+    with pytest.raises(PgsgdError, match="set_coords"):
+        G.layout(T)
+    far = g.init_xy.copy()
+    far[3, 0] = 2.0 ** 31
+    with pytest.raises(PgsgdError, match="2\\^30"):
+        G.set_coords(far)
+    with pytest.raises(PgsgdError, match="theta"):
+        G.set_coords(g.init_xy)
+        G.layout(T, theta=5.0)

@@ -1,0 +1,222 @@
+"""CUDA path against the CPU oracle, through the C ABI.
+
+Three parity levels: the drawn pairs are bit-exact, a Jacobi sweep of moves
+from a frozen layout agrees with the FP64 oracle to 1e-5 of each move's
+scale, and the sampled-stress kernel agrees with the oracle's Eq. 2 on the
+same layout and sample set. Sizes run from a few steps (ragged, empty and
+one-step paths) over several thread blocks up to the 5 M-node chromosome
+graph in the benchmark's launch configuration (sampled update ranges there).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from synth import make_custom, make_graph
+
+pytestmark = pytest.mark.gpu
+
+T = 30
+THETA = 0.99
+
+
+@pytest.fixture(scope="module")
+def pg():
+    import paper_2409_00876_gb300 as pg
+    pg.load_library()
+    return pg
+
+
+_graphs = {}
+
+
+def _graph(name):
+    if name not in _graphs:
+        if name == "ragged":
+            lens = [3, 1, 7, 2, 5, 1, 9, 4, 6, 2]
+            paths = [[(0, 0), (1, 0), (2, 1), (3, 0), (1, 0)], [], [(4, 0)],
+                     [(5, 1), (6, 0)], [(v % 10, v % 2) for v in range(37)], [(7, 0), (7, 1)]]
+            _graphs[name] = make_custom(lens, paths, seed=3)
+        else:
+            _graphs[name] = make_graph(name)
+    return _graphs[name]
+
+
+def _gpu_graph(pg, g, **opts):
+    G = pg.Graph.from_synth(g)
+    for k, v in opts.items():
+        G.set_option(k, v)
+    G.set_coords(g.init_xy)
+    return G
+
+
+def _compare_samples(a, b):
+    for f in ("g", "path", "i", "j", "cooling", "e_i", "e_j", "skip", "d_ref"):
+        np.testing.assert_array_equal(a[f], b[f], err_msg=f)
+
+
+# ------------------------------------------------------------------ level 1: draws
+
+@pytest.mark.parametrize("name", ["ragged", "tiny", "mid"])
+@pytest.mark.parametrize("t", [0, 7, 14, 15, 29])
+def test_pairs_bit_exact(pg, name, t):
+    g = _graph(name)
+    G = _gpu_graph(pg, g)
+    n = min(10 * g.n_steps, 300_000)
+    for seed in (1, 0xDEADBEEFCAFEF00D):
+        got = G.debug_sample(t, T, THETA, seed, 12345, n)
+        want = O.sample(g, T, t, THETA, seed, 12345, n)
+        _compare_samples(got, want)
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.5, 1.0, 1.7, 3.5])
+def test_pairs_bit_exact_other_theta(pg, theta):
+    g = _graph("mid")
+    G = _gpu_graph(pg, g)
+    got = G.debug_sample(20, T, theta, 5, 0, 200_000)
+    want = O.sample(g, T, 20, theta, 5, 0, 200_000)
+    _compare_samples(got, want)
+
+
+def test_pairs_bit_exact_odd_schedule_and_high_counter(pg):
+    g = _graph("tiny")
+    G = _gpu_graph(pg, g)
+    u0 = (1 << 32) - 1000  # the counter's high word changes inside the range
+    for t in (15, 16):
+        got = G.debug_sample(t, 31, THETA, 9, u0, 5000)
+        want = O.sample(g, 31, t, THETA, 9, u0, 5000)
+        _compare_samples(got, want)
+
+
+# ------------------------------------------------------------------ level 2: Jacobi sweep
+
+def _sweep_check(G, g, xy, t, eta, seed, u0, count):
+    got = G.debug_sweep(t, T, eta, THETA, seed, u0, count).astype(np.float64)
+    want = O.sweep(g, xy, T, t, eta, THETA, seed, u0, count)
+    s = O.sample(g, T, t, THETA, seed, u0, count)
+    off = g.path_off.astype(np.int64)[s["path"]]
+    ni = g.step_node[off + s["i"].astype(np.int64)]
+    nj = g.step_node[off + s["j"].astype(np.int64)]
+    vi = xy[ni, 0:2].copy()
+    vi[s["e_i"] == 1] = xy[ni[s["e_i"] == 1], 2:4]
+    vj = xy[nj, 0:2].copy()
+    vj[s["e_j"] == 1] = xy[nj[s["e_j"] == 1], 2:4]
+    mag = np.hypot(*(vi - vj).T)
+    d = s["d_ref"].astype(np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        mu = np.minimum(eta / (d * d), 1.0)
+    scale = np.where(s["skip"] == 0, mu * (mag + d) / 2, 0.0)
+    err = np.abs(got - want).max(axis=1)
+    # per update: |dv_gpu - dv_ref| <= 1e-5 * mu (|v_i - v_j| + d_ref) / 2
+    bad = err > 1e-5 * scale + 1e-30
+    assert not bad.any(), (np.nonzero(bad)[0][:5], err[bad][:5], scale[bad][:5])
+    # skipped updates move nothing on both sides
+    assert np.all(got[s["skip"] != 0] == 0) and np.all(want[s["skip"] != 0] == 0)
+    # normwise over the sweep
+    assert np.linalg.norm(got - want) <= 1e-5 * np.linalg.norm(want)
+
+
+@pytest.mark.parametrize("name", ["ragged", "tiny", "mid"])
+@pytest.mark.parametrize("t", [0, 12, 29])
+def test_jacobi_sweep_within_1e5(pg, name, t):
+    g = _graph(name)
+    G = _gpu_graph(pg, g)
+    xy = G.get_coords()  # the exact value of the stored representation
+    eta = O.eta_schedule(T, O.default_eta_max(g))[t]
+    _sweep_check(G, g, xy, t, eta, 3, 777, min(10 * g.n_steps, 200_000))
+
+
+def test_jacobi_sweep_from_laid_out_layout(pg):
+    g = _graph("mid")
+    G = _gpu_graph(pg, g)
+    G.layout(T, theta=THETA, seed=4, iter_end=20)
+    xy = G.get_coords()
+    eta = O.eta_schedule(T, O.default_eta_max(g))[25]
+    _sweep_check(G, g, xy, 25, eta, 8, 0, 200_000)
+
+
+# ------------------------------------------------------------------ level 3: stress kernel
+
+@pytest.mark.parametrize("name", ["ragged", "tiny", "mid"])
+def test_stress_kernel_matches_oracle_on_same_layout(pg, name):
+    g = _graph(name)
+    G = _gpu_graph(pg, g)
+    if name != "ragged":
+        G.layout(T, theta=THETA, seed=2, iter_end=5)
+    xy = G.get_coords()
+    per = 100 if name != "mid" else 10
+    got = G.stress(per, seed=11, per_path=True)
+    want = O.sampled_stress(g, xy, per_step=per, seed=11, per_path=True)
+    assert got["n_valid"] == want["n_valid"]
+    assert got["n_skipped"] == want["n_skipped"]
+    assert abs(got["mean"] - want["mean"]) <= 1e-4 * want["mean"]
+    assert abs(got["std"] - want["std"]) <= 1e-3 * want["std"]
+    np.testing.assert_array_equal(got["per_path"][:, 2], want["per_path"][:, 2])
+    np.testing.assert_allclose(got["per_path"][:, 0], want["per_path"][:, 0], rtol=1e-4, atol=1e-12)
+
+
+def test_coords_round_trip_exact(pg):
+    g = _graph("tiny")
+    for mode in (0, 1):
+        G = pg.Graph.from_synth(g)
+        G.set_option("coord_mode", mode)
+        G.set_coords(g.init_xy)
+        np.testing.assert_array_equal(G.get_coords(), g.init_xy)  # FP32-representable input
+
+
+def test_coords_device_tensors(pg):
+    import torch
+    g = _graph("tiny")
+    G = pg.Graph.from_synth(g)
+    G.set_coords(torch.from_numpy(g.init_xy).cuda())
+    out = torch.empty((g.n_nodes, 4), dtype=torch.float64, device="cuda")
+    G.get_coords(out)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), g.init_xy)
+
+
+def test_graph_from_device_tensors_matches_host(pg):
+    import torch
+    g = _graph("tiny")
+    Gd = pg.Graph(*[torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in
+                    (g.node_len, g.path_off, g.step_node, g.step_rev, g.step_pos)])
+    Gd.set_coords(g.init_xy)
+    Gh = _gpu_graph(pg, g)
+    _compare_samples(Gd.debug_sample(3, T, THETA, 1, 0, 50_000), Gh.debug_sample(3, T, THETA, 1, 0, 50_000))
+
+
+# ------------------------------------------------------------------ full-size, sampled
+
+@pytest.fixture(scope="module")
+def chrom(pg):
+    g = _graph("chrom")
+    G = _gpu_graph(pg, g)
+    return g, G
+
+
+def test_chromosome_pairs_bit_exact_sampled_ranges(chrom):
+    g, G = chrom
+    N = 10 * g.n_steps
+    for t, u0 in [(0, 0), (3, N // 3), (14, N - 100_000), (20, N // 2 + 17), (29, (1 << 32) - 50_000)]:
+        got = G.debug_sample(t, T, THETA, 1, u0, 100_000)
+        want = O.sample(g, T, t, THETA, 1, u0, 100_000)
+        _compare_samples(got, want)
+
+
+def test_chromosome_jacobi_sweep_sampled_ranges(chrom):
+    g, G = chrom
+    xy = G.get_coords()
+    eta = O.eta_schedule(T, O.default_eta_max(g))
+    N = 10 * g.n_steps
+    for t, u0 in [(0, N // 5), (16, N // 2), (29, N - 60_000)]:
+        _sweep_check(G, g, xy, t, eta[t], 1, u0, 50_000)
+
+
+def test_chromosome_stress_kernel_sampled_paths(chrom):
+    g, G = chrom
+    xy = G.get_coords()
+    got = G.stress(1, seed=3, per_path=True)
+    # the oracle evaluates the same samples of a subset of paths one by one
+    for p in [0, 1, 44, 89]:
+        want = O.sampled_stress(g, xy, per_step=1, seed=3, per_path=True, paths=(p, p + 1))
+        assert got["per_path"][p, 2] == want["per_path"][p, 2]
+        assert abs(got["per_path"][p, 0] - want["per_path"][p, 0]) <= 1e-4 * want["per_path"][p, 0]
