@@ -46,6 +46,8 @@ WORKLOADS = {
              "tail to 100 kb; 30 iterations x 10 x steps updates; theta 0.99",
     "mid": "synthetic pangenome: 200,000 backbone nodes, 32 paths, ~7e6 steps",
     "tiny": "synthetic pangenome: 2,000 backbone nodes, 8 paths, ~1.6e4 steps",
+    "prof": "synthetic chromosome-like pangenome for profiling: 2,000,000 backbone nodes, "
+            "30 paths, ~6.3e7 steps (0.6 GB on device, above L2)",
 }
 
 
@@ -160,6 +162,8 @@ class ClockSampler:
 
 def make_workload(config):
     from synth import make_graph
+    if config == "prof":
+        return make_graph("chrom", backbone=2_000_000, paths=30)
     return make_graph(config)
 
 
@@ -334,16 +338,31 @@ def run_e2e(pg, g, args, dev):
     h2d = sum(t.numel() * t.element_size() for t in host.values()) + xy_in.numel() * 8
     d2h = xy_out.numel() * 8 + 48
 
+    phases = {}
+
+    def mark(name, t0):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        phases[name] = phases.get(name, 0.0) + (t1 - t0)
+        return t1
+
     def one():
+        t = time.perf_counter()
         G = pg.Graph(host["node_len"].numpy(), host["path_off"].numpy(), host["step_node"].numpy(),
                      host["step_rev"].numpy(), host["step_pos"].numpy())
+        t = mark("create_s", t)
         G.set_coords(xy_in.numpy())
+        t = mark("set_coords_s", t)
         G.layout(ITERS, theta=THETA, seed=SEED)
+        t = mark("layout_s", t)
         G.stress(STRESS_PER_STEP, seed=STRESS_SEED)
+        t = mark("stress_s", t)
         G.get_coords(xy_out.numpy())
         G.close()
+        mark("get_coords_close_s", t)
 
     one()
+    phases.clear()
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
@@ -353,7 +372,8 @@ def run_e2e(pg, g, args, dev):
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     return {"unit": UNIT, "updates": ITERS * 10 * g.n_steps * k, "seconds": dt, "steps": k,
-            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "phases_s_per_step": {n: round(v / k, 3) for n, v in phases.items()}}
 
 
 def kernel_revision():

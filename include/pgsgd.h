@@ -42,25 +42,30 @@ typedef enum pgsgd_status {
 
 /* Options for pgsgd_set_option / pgsgd_get_option. */
 typedef enum pgsgd_option {
-    /* Coordinate storage. 0 = anchored (default): each node keeps an integer
-     * anchor per axis and FP32 offsets from it, so FP32 keeps sub-nucleotide
-     * resolution at chromosome scale (coordinates up to about 1e9).
+    /* Coordinate storage. 0 = anchored (default): a node whose coordinate on
+     * an axis is at least 4096 in magnitude keeps an integer anchor on that
+     * axis and FP32 offsets from it, so FP32 keeps sub-nucleotide resolution
+     * at chromosome scale (coordinates below 2^30).
      * 1 = plain FP32 absolute coordinates. Takes effect at pgsgd_set_coords. */
     PGSGD_OPT_COORD_MODE = 1,
     /* Updates per iteration = this value times the number of path steps
      * (Algorithm 1, line 1 uses 10). Default 10. */
     PGSGD_OPT_UPDATES_PER_STEP = 2,
-    /* Update-kernel launch shape: threads per block (64..1024, multiple of
-     * 32; default 256), resident blocks per SM in the grid (default 8), and
+    /* Update-kernel launch shape: threads per block (64..256, multiple of
+     * 32; default 256), blocks per SM in the grid (default 8), and
      * updates each thread keeps in flight per loop trip (1, 2 or 4; default 2). */
     PGSGD_OPT_BLOCK = 3,
     PGSGD_OPT_BLOCKS_PER_SM = 4,
     PGSGD_OPT_UPDATES_PER_THREAD = 5,
     /* 0 = plain stores of the moved points (last writer wins, as in the
-     * paper's kernels; default), 1 = vector atomic adds of the moves. */
+     * paper's kernels; default), 1 = vector atomic adds of the moves. Atomic
+     * adds sum colliding full-rate (mu = 1) moves, which overshoot; on small
+     * graphs under a full grid that diverges, so keep 0 unless the
+     * concurrency cap makes collisions rare. */
     PGSGD_OPT_ATOMIC_UPDATES = 6,
-    /* 1 = after each iteration, move every anchor to the rounded current
-     * start point so the FP32 offsets stay small (anchored mode; default 1). */
+    /* 1 = after each iteration, move the anchor of every node whose start
+     * offset has drifted past 8 to the rounded start point, so the FP32
+     * offsets stay small (anchored mode; default 1). */
     PGSGD_OPT_REBASE = 7,
     /* 1 = record CUDA events around every update-kernel launch on the
      * launching stream; read them with pgsgd_timing_read. Default 0. */
@@ -68,7 +73,23 @@ typedef enum pgsgd_option {
     /* Concurrency cap: the update kernel's grid is shrunk so that at most this
      * many updates are in flight at once (0 = no cap). Small graphs under a
      * full GB300 grid would otherwise see many simultaneous updates per node. */
-    PGSGD_OPT_MAX_CONCURRENT = 9
+    PGSGD_OPT_MAX_CONCURRENT = 9,
+    /* Register budget of the update kernel: the number of resident 256-thread
+     * blocks per SM its registers must allow (1 = compiler's choice; the
+     * compiled variants are 1, 4, 6 for 1 update per thread, 1, 3, 4 for 2
+     * and 1, 2, 3 for 4). Default 1. */
+    PGSGD_OPT_MIN_BLOCKS = 10,
+    /* L2 fetch granularity in bytes set on the current context before each
+     * layout (cudaLimitMaxL2FetchGranularity; 0 = leave it unchanged, the
+     * default). Every access of the path is a random 32-byte sector. */
+    PGSGD_OPT_L2_FETCH = 11,
+    /* How a moved point is written when atomic updates are off: 0 = plain
+     * store, 1 = st.cg, 2 = st.cs, 3 = st.wt, 4 = st.relaxed.gpu,
+     * 5 = st.L1::no_allocate, 6 = 64-bit atomic exchange (default). All
+     * replace the point (last writer wins, the paper's racy store); on GB300
+     * the exchange, executed at L2, ran 1.4x (5 M-node graph) to 7x
+     * (200 k-node graph) faster than every plain-store form. */
+    PGSGD_OPT_STORE_MODE = 12
 } pgsgd_option;
 
 /* Device-resident graph: node records, packed step records, path table. */

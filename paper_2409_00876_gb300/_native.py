@@ -17,7 +17,8 @@ u8, u32, u64, i32, i64, dbl = C.c_uint8, C.c_uint32, C.c_uint64, C.c_int, C.c_in
 PGSGD_OK, PGSGD_EINVAL, PGSGD_ERANGE, PGSGD_ENOMEM, PGSGD_ECUDA, PGSGD_ETIMEOUT, PGSGD_EDEVICE = range(7)
 
 OPT = dict(coord_mode=1, updates_per_step=2, block=3, blocks_per_sm=4, updates_per_thread=5,
-           atomic_updates=6, rebase=7, timing=8, max_concurrent=9)
+           atomic_updates=6, rebase=7, timing=8, max_concurrent=9,
+           min_blocks=10, l2_fetch=11, store_mode=12)
 
 
 class StressResult(C.Structure):

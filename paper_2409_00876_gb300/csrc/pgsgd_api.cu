@@ -51,6 +51,9 @@ struct pgsgd_graph {
     int rebase = 1;
     int timing = 0;
     int64_t max_concurrent = -1;  // -1 = automatic
+    int min_blocks = 1;
+    int l2_fetch = 0;
+    int store_mode = 6;  // 64-bit atomic exchange: measured fastest replace-store
 
     // timing
     std::vector<cudaEvent_t> ev_free;
@@ -356,7 +359,7 @@ int pgsgd_set_option(pgsgd_graph* g, int option, int64_t v) {
             g->updates_per_step = (int)v;
             return PGSGD_OK;
         case PGSGD_OPT_BLOCK:
-            if (v < 64 || v > 1024 || v % 32) return fail(PGSGD_EINVAL, "block must be 64..1024, multiple of 32");
+            if (v < 64 || v > 256 || v % 32) return fail(PGSGD_EINVAL, "block must be 64..256, multiple of 32");
             g->block = (int)v;
             return PGSGD_OK;
         case PGSGD_OPT_BLOCKS_PER_SM:
@@ -380,6 +383,19 @@ int pgsgd_set_option(pgsgd_graph* g, int option, int64_t v) {
             if (v < -1) return fail(PGSGD_EINVAL, "max concurrent must be >= -1");
             g->max_concurrent = v;
             return PGSGD_OK;
+        case PGSGD_OPT_MIN_BLOCKS:
+            if (v < 1 || v > 6) return fail(PGSGD_EINVAL, "min blocks must be in [1, 6]");
+            g->min_blocks = (int)v;
+            return PGSGD_OK;
+        case PGSGD_OPT_STORE_MODE:
+            if (v < 0 || v > 6) return fail(PGSGD_EINVAL, "store mode must be in [0, 6]");
+            g->store_mode = (int)v;
+            return PGSGD_OK;
+        case PGSGD_OPT_L2_FETCH:
+            if (v != 0 && v != 32 && v != 64 && v != 128)
+                return fail(PGSGD_EINVAL, "L2 fetch granularity must be 0, 32, 64 or 128");
+            g->l2_fetch = (int)v;
+            return PGSGD_OK;
         default:
             return fail(PGSGD_EINVAL, "unknown option %d", option);
     }
@@ -397,6 +413,9 @@ int pgsgd_get_option(const pgsgd_graph* g, int option, int64_t* v) {
         case PGSGD_OPT_REBASE: *v = g->rebase; return PGSGD_OK;
         case PGSGD_OPT_TIMING: *v = g->timing; return PGSGD_OK;
         case PGSGD_OPT_MAX_CONCURRENT: *v = g->max_concurrent; return PGSGD_OK;
+        case PGSGD_OPT_MIN_BLOCKS: *v = g->min_blocks; return PGSGD_OK;
+        case PGSGD_OPT_L2_FETCH: *v = g->l2_fetch; return PGSGD_OK;
+        case PGSGD_OPT_STORE_MODE: *v = g->store_mode; return PGSGD_OK;
         default: return fail(PGSGD_EINVAL, "unknown option %d", option);
     }
 }
@@ -494,7 +513,10 @@ int pgsgd_layout(pgsgd_graph* g, uint32_t iter_max, const double* eta, double et
     L.block = g->block;
     L.grid = grid;
     L.upt = g->upt;
+    L.minb = g->min_blocks;
+    L.store_mode = g->store_mode;
     L.atomic = g->atomic != 0;
+    if (g->l2_fetch) CK(cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, g->l2_fetch), "L2 fetch limit");
     for (uint32_t t = iter_begin; t < iter_end; ++t) {
         L.s = sampler_args(g, iter_max, t, th, seed);
         L.eta = (float)sched[t];

@@ -47,9 +47,13 @@ __device__ __forceinline__ int64_t endpoint_pos(uint64_t s, uint32_t e, uint32_t
 
 // ---------------------------------------------------------------- memory access
 
-// Packed step records are read-only during a launch: non-coherent path.
+// Packed step records: one random 8-byte read per record. Read at L2 (.cg)
+// so the request is a single 32-byte sector; through the L1/texture path an
+// isolated miss pulled the whole 128-byte line from L2 and DRAM.
 __device__ __forceinline__ uint64_t load_step(const uint64_t* p) {
-    return __ldg(reinterpret_cast<const unsigned long long*>(p));
+    uint64_t v;
+    asm volatile("ld.global.cg.u64 %0, [%1];" : "=l"(v) : "l"(p));
+    return v;
 }
 
 // Node records change during a launch (Hogwild!): read them from L2 (.cg),

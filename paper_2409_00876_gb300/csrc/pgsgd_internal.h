@@ -28,7 +28,8 @@ struct UpdateLaunch {
     uint64_t u_begin;    // first update index
     uint64_t n_updates;  // updates in this launch
     float eta;
-    int block, grid, upt;
+    int block, grid, upt, minb;
+    int store_mode;
     bool atomic;
 };
 

@@ -92,12 +92,14 @@ __global__ void set_coords_kernel(const double* __restrict__ xy, NodeRec* __rest
         NodeRec r = nodes[v];
         int32_t ax = 0, ay = 0;
         if (anchored) {
+            // Anchor an axis only where FP32 would lose sub-nucleotide
+            // resolution; below 4096 the FP32 value itself is kept exactly.
             const double lim = 1073741824.0;  // 2^30
             if (fabs(sx) >= lim || fabs(sy) >= lim || fabs(ex) >= lim || fabs(ey) >= lim)
                 bad |= FLAG_COORD_RANGE;
             else {
-                ax = (int32_t)rint(sx);
-                ay = (int32_t)rint(sy);
+                ax = fabs(sx) >= 4096.0 ? (int32_t)rint(sx) : 0;
+                ay = fabs(sy) >= 4096.0 ? (int32_t)rint(sy) : 0;
             }
         }
         r.ax = ax;
@@ -123,8 +125,10 @@ __global__ void get_coords_kernel(const NodeRec* __restrict__ nodes, double* __r
     }
 }
 
-// Move each anchor to the rounded start point so offsets stay near zero.
-// Subtracting an integer within half a unit of sx leaves sx exact.
+// Move an anchor to the rounded start point once its offset has drifted past
+// 8, so offsets stay small: an FP32 offset below 8 resolves 1e-6 nt, while one
+// near 4096 would only resolve 2.4e-4 nt. Subtracting an integer within half
+// a unit of sx leaves sx exact.
 __global__ void rebase_kernel(NodeRec* __restrict__ nodes, uint32_t n) {
     for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
          v += (uint64_t)gridDim.x * blockDim.x) {
@@ -205,6 +209,23 @@ __device__ __forceinline__ Move pair_move(const NodeRec& a, uint32_t ea, const N
     return m;
 }
 
+// Write one moved point (8 bytes). The cache operator is selectable.
+__device__ __forceinline__ void store_point(float* p, float x, float y, int mode) {
+    switch (mode) {
+        case 1: asm volatile("st.global.cg.v2.f32 [%0], {%1, %2};" :: "l"(p), "f"(x), "f"(y) : "memory"); break;
+        case 2: asm volatile("st.global.cs.v2.f32 [%0], {%1, %2};" :: "l"(p), "f"(x), "f"(y) : "memory"); break;
+        case 3: asm volatile("st.global.wt.v2.f32 [%0], {%1, %2};" :: "l"(p), "f"(x), "f"(y) : "memory"); break;
+        case 4: asm volatile("st.relaxed.gpu.global.v2.f32 [%0], {%1, %2};" :: "l"(p), "f"(x), "f"(y) : "memory"); break;
+        case 5: asm volatile("st.global.L1::no_allocate.v2.f32 [%0], {%1, %2};" :: "l"(p), "f"(x), "f"(y) : "memory"); break;
+        case 6: {  // exchange: an atomic that replaces instead of adding
+            unsigned long long v = ((unsigned long long)__float_as_uint(y) << 32) | __float_as_uint(x);
+            atomicExch(reinterpret_cast<unsigned long long*>(p), v);
+            break;
+        }
+        default: *reinterpret_cast<float2*>(p) = make_float2(x, y); break;
+    }
+}
+
 // ---------------------------------------------------------------- the update kernel
 
 // One launch = one iteration's N updates (or a slice), grid-stride over the
@@ -212,8 +233,9 @@ __device__ __forceinline__ Move pair_move(const NodeRec& a, uint32_t ea, const N
 // loop trip: all draws first (ALU), then all step-record loads, then all
 // node-record loads, then the moves, so that 2 * UPT DRAM requests per
 // thread overlap instead of queueing behind each other.
-template <int UPT, bool ATOMIC>
-__global__ void update_kernel(UpdateLaunch L) {
+template <int UPT, int MINB>
+__global__ void __launch_bounds__(256, MINB) update_kernel(UpdateLaunch L) {
+    const bool ATOMIC = L.atomic;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ ZipfConsts zc;
     const PathTable pt = stage_paths(L.s, smem, zc);
@@ -269,8 +291,8 @@ __global__ void update_kernel(UpdateLaunch L) {
             } else {
                 const float xa = ea ? na[k].ex : na[k].sx, ya = ea ? na[k].ey : na[k].sy;
                 const float xb = eb ? nb[k].ex : nb[k].sx, yb = eb ? nb[k].ey : nb[k].sy;
-                *reinterpret_cast<float2*>(pa_ptr) = make_float2(xa + m.dxi, ya + m.dyi);
-                *reinterpret_cast<float2*>(pb_ptr) = make_float2(xb + m.dxj, yb + m.dyj);
+                store_point(pa_ptr, xa + m.dxi, ya + m.dyi, L.store_mode);
+                store_point(pb_ptr, xb + m.dxj, yb + m.dyj, L.store_mode);
             }
         }
     }
@@ -543,25 +565,31 @@ cudaError_t launch_zipf_setup(const uint64_t* path_off, uint32_t n_paths, float 
     return cudaGetLastError();
 }
 
-template <int UPT, bool ATOMIC>
+template <int UPT, int MINB>
 static cudaError_t launch_update_t(const UpdateLaunch& L, cudaStream_t st) {
     const size_t smem = update_smem_bytes(L.s.n_paths);
-    cudaError_t e = cudaFuncSetAttribute(update_kernel<UPT, ATOMIC>,
+    cudaError_t e = cudaFuncSetAttribute(update_kernel<UPT, MINB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    update_kernel<UPT, ATOMIC><<<L.grid, L.block, smem, st>>>(L);
+    update_kernel<UPT, MINB><<<L.grid, L.block, smem, st>>>(L);
     return cudaGetLastError();
 }
 
+// UPT = updates in flight per thread; MINB = resident 256-thread blocks per
+// SM the register allocation must allow (1 = unconstrained).
 cudaError_t launch_update(const UpdateLaunch& L, cudaStream_t st) {
     if (L.n_updates == 0) return cudaSuccess;
-    switch (L.upt * 2 + (L.atomic ? 1 : 0)) {
-        case 2: return launch_update_t<1, false>(L, st);
-        case 3: return launch_update_t<1, true>(L, st);
-        case 4: return launch_update_t<2, false>(L, st);
-        case 5: return launch_update_t<2, true>(L, st);
-        case 8: return launch_update_t<4, false>(L, st);
-        case 9: return launch_update_t<4, true>(L, st);
+    if (L.block > 256 && L.minb > 1) return cudaErrorInvalidValue;
+    switch (L.upt * 10 + L.minb) {
+        case 11: return launch_update_t<1, 1>(L, st);
+        case 14: return launch_update_t<1, 4>(L, st);
+        case 16: return launch_update_t<1, 6>(L, st);
+        case 21: return launch_update_t<2, 1>(L, st);
+        case 23: return launch_update_t<2, 3>(L, st);
+        case 24: return launch_update_t<2, 4>(L, st);
+        case 41: return launch_update_t<4, 1>(L, st);
+        case 42: return launch_update_t<4, 2>(L, st);
+        case 43: return launch_update_t<4, 3>(L, st);
         default: return cudaErrorInvalidValue;
     }
 }
