@@ -6,7 +6,7 @@
  * The method is the one of "Rapid GPU-Based Pangenome Graph Layout" (SC24):
  * Algorithm 1 (Section II-C) moves the two endpoints of randomly chosen
  * same-path node pairs towards their path distance, millions of times per
- * iteration, without locks (Hogwild!, Section III-A); Eq. 2 (Section V-B)
+ * iteration, without locks (Hogwild!, Section III-A); Eq. 2 (Section VI-B)
  * scores a layout by sampling such pairs.
  *
  * Conventions for every entry point:
@@ -95,7 +95,7 @@ typedef enum pgsgd_option {
 /* Device-resident graph: node records, packed step records, path table. */
 typedef struct pgsgd_graph pgsgd_graph;
 
-/* Result of pgsgd_stress (Eq. 2 and the interval of Section V-B). */
+/* Result of pgsgd_stress (Eq. 2 and the interval of Section VI-B). */
 typedef struct pgsgd_stress_result {
     double mean;        /* sampled path stress: sum of terms / n_valid */
     double stddev;      /* sample standard deviation of the terms */
@@ -132,7 +132,7 @@ typedef struct pgsgd_info {
 
 /*
  * Build the device-resident graph (Section II-A: nodes with sequence lengths
- * and paths that walk them; Section IV-B1: only the fields the layout reads).
+ * and paths that walk them; Section V-A: only the fields the layout reads).
  *
  *   node_len[n_nodes]        sequence length of every node, >= 1
  *   path_off[n_paths + 1]    path p owns steps [path_off[p], path_off[p+1]);
@@ -195,7 +195,7 @@ int pgsgd_layout(pgsgd_graph *g, uint32_t iter_max, const double *eta,
                  uint32_t iter_begin, uint32_t iter_end, void *cuda_stream);
 
 /*
- * Sampled path stress of the current layout (Eq. 2, Section V-B): for every
+ * Sampled path stress of the current layout (Eq. 2, Section VI-B): for every
  * path p with at least two steps, samples_per_step * |p| pairs (the paper
  * uses 100): step i uniform, step j uniform among the others, a coin for
  * each endpoint; the term ((|v_i - v_j| - d_ref) / d_ref)^2 in FP32, summed

@@ -22,9 +22,9 @@
  *     threaded mode runs the inner loop on several threads with unsynchronised
  *     (relaxed atomic) loads and stores of the coordinates. One thread gives
  *     the sequential definition.
- *   - Eq. 1 (Section V-A): path stress, every same-path node pair averaged over
+ *   - Eq. 1 (Section VI-A): path stress, every same-path node pair averaged over
  *     its four endpoint combinations.
- *   - Eq. 2 (Section V-B): sampled path stress over 100 |p| pairs per path and
+ *   - Eq. 2 (Section VI-B): sampled path stress over 100 |p| pairs per path and
  *     its 95 % confidence interval mu +- 1.96 sigma / sqrt(n), sigma from a
  *     second pass over the same samples.
  *

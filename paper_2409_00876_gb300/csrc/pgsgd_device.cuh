@@ -21,7 +21,7 @@ namespace pgsgd {
 // a node is drawn as a line segment) as FP32 offsets from an integer anchor
 // per axis, plus the sequence length the reference distances need. 32 bytes,
 // 32-byte aligned: one DRAM sector holds a whole node (the cache-friendly
-// node record of Section IV-B1, sized to a Blackwell sector).
+// node record of Section V-B1, sized to a Blackwell sector).
 struct __align__(32) NodeRec {
     float sx, sy, ex, ey;  // start x, start y, end x, end y (offsets)
     int32_t ax, ay;        // anchors (0 in plain-FP32 mode)

@@ -1,7 +1,7 @@
 """Seeded synthetic pangenome graphs shaped like the paper's workloads.
 
 The paper lays out HPRC chromosome graphs and the HLA-DRB1 / MHC graphs
-(Section IV, Table I; Section VII-A, Table VI). None of those datasets is
+(Section III, Table I; Section VII-A, Table VI). None of those datasets is
 available here, so these generators stand in for them. A graph is a linear
 backbone of nodes that every path follows, with the variation the paper's
 Section II-A describes:

@@ -78,7 +78,7 @@ def test_single_path_sampled_stress_is_unbiased_for_all_pair_average():
 
 
 def test_sampled_stress_tracks_full_stress_across_layouts():
-    # Section V-B, Fig. 11: sampled path stress follows path stress over
+    # Section VI-B, Fig. 11: sampled path stress follows path stress over
     # layouts of different quality (r = 0.995 in the paper)
     g = make_graph("tiny", backbone=300, paths=4)
     rng = np.random.default_rng(1)
