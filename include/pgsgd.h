@@ -238,6 +238,37 @@ int pgsgd_debug_sweep(pgsgd_graph *g, uint32_t t, uint32_t iter_max, double eta,
 int pgsgd_timing_read(pgsgd_graph *g, double *total_ms, uint64_t *launches,
                       uint64_t *updates, int reset);
 
+/*
+ * Sampled path stress without any device allocation. The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc, for example code whose device memory is owned entirely by
+ * another allocator or a fixed preallocated budget (an embedding framework
+ * that forbids outside allocations), or code that must not allocate at the
+ * point of the call. It computes the same statistic as pgsgd_stress (same
+ * samples for the same seed, FP32 terms, FP64 sums) straight from the
+ * caller's raw arrays, with no graph handle:
+ *   node_len, path_off, step_node, step_rev, step_pos   as for pgsgd_create,
+ *                        all in DEVICE memory, already valid (not checked)
+ *   xy[n_nodes][4]       float64 layout in DEVICE memory
+ *   out                  one pgsgd_stress_result in DEVICE memory, written by
+ *                        the last kernel of the call
+ * Asynchronous on cuda_stream; the caller synchronises before reading *out.
+ * Scratch: a fixed file-scope device array of 96 KiB that every GPU which
+ * loads the library holds until the process exits; it has room for the
+ * partial sums of 4096 blocks (the grid is capped there). Limit:
+ * n_paths <= 8192 (PGSGD_ERANGE beyond, with a message). The first call on a
+ * device looks up the array's device address and sets the kernel's shared
+ * memory limit, so make that first call before any stream capture. All calls
+ * share the array (each call writes every slot it reads, so nothing is
+ * cleared): calls that overlap on the GPU, on any streams, race on it.
+ */
+int pgsgd_stress_noalloc(const uint32_t *node_len, uint32_t n_nodes,
+                         const uint64_t *path_off, uint32_t n_paths,
+                         const uint32_t *step_node, const uint8_t *step_rev,
+                         const int64_t *step_pos, const double *xy,
+                         uint32_t samples_per_step, uint64_t seed,
+                         pgsgd_stress_result *out, void *cuda_stream);
+
 /* Message of the calling thread's last failure ("" if none). */
 const char *pgsgd_last_error(void);
 

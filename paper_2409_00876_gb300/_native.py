@@ -51,6 +51,7 @@ _SIGS = {
     "pgsgd_debug_sample": ([P, u32, u32, dbl, u64, u64, u64, P, P], i32),
     "pgsgd_debug_sweep": ([P, u32, u32, dbl, dbl, u64, u64, u64, P, P], i32),
     "pgsgd_timing_read": ([P, P, P, P, i32], i32),
+    "pgsgd_stress_noalloc": ([P, u32, P, u32, P, P, P, P, u32, u64, P, P], i32),
     "pgsgd_last_error": ([], C.c_char_p),
     "pgsgd_status_string": ([i32], C.c_char_p),
 }

@@ -78,6 +78,20 @@ int fail(int status, const char* fmt, ...) {
     return status;
 }
 
+}  // namespace
+
+int pgsgd::report_error(int status, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return status;
+}
+
+namespace {
+
 int cuda_fail(cudaError_t e, const char* what) {
     return fail(e == cudaErrorMemoryAllocation ? PGSGD_ENOMEM : PGSGD_ECUDA, "%s: %s (%s)", what,
                 cudaGetErrorString(e), cudaGetErrorName(e));

@@ -75,4 +75,8 @@ cudaError_t launch_debug_sweep(const SamplerArgs& s, uint64_t u_begin, uint64_t 
 cudaError_t launch_stress(const StressLaunch& L, cudaStream_t st);
 cudaError_t launch_stress_finalize(const double* partials, int n, double* out3, cudaStream_t st);
 
+// Record the calling thread's error message (read by pgsgd_last_error) and
+// return status.
+int report_error(int status, const char* fmt, ...);
+
 }  // namespace pgsgd
