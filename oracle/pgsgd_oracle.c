@@ -32,8 +32,9 @@
  *   - Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key
  *     (seed_lo, seed_hi). Update u of iteration t uses counter
  *     (u_lo, u_hi, t, b) for block b = 0, 1, ...; words w0..w3 come from block
- *     0, w4..w7 from block 1 and so on. Stress sample q of path p uses counter
- *     (q_lo, q_hi, 0x80000000 | p, b) under the stress seed.
+ *     0, and further blocks only when the power-law draw rejects. Stress
+ *     sample q of path p uses counter (q_lo, q_hi, 0x80000000 | p, 0) under
+ *     the stress seed.
  *   - Step i: g = mulhi64(w0 | w1 << 32, S); p is the path whose step range
  *     holds g; i = g - off[p]. This is "p with probability |p| / S, then i
  *     uniform in p". Paths with fewer than two steps give no update.
@@ -42,12 +43,14 @@
  *     rejection-inversion (Hoermann and Derflinger, ACM TOMACS 6(3), 1996)
  *     evaluated in IEEE binary32 with the operation order fixed below (no
  *     fused multiply-add anywhere; a draw with k >= 256 is accepted without
- *     the rejection test), one 32-bit word per trial: w4, w5, w6, w7,
- *     then block 2, and so on, at most 64 trials (then k = 1). Direction bit
+ *     the rejection test), one 32-bit word per trial: w3, then the four words
+ *     of block 1, block 2 and so on, at most 64 trials (then k = 1). Direction bit
  *     (w2 >> 1) & 1: 1 = forward (j = i + k), 0 = backward (j = i - k); if that
  *     leaves the path the other direction is used; if both leave it, j is the
  *     path end farther from i.
- *   - Uniform: x = mulhi64(w4 | w5 << 32, n_p - 1); j = x + (x >= i).
+ *   - Uniform: r = w3 << 32 | (w2 & ~15) (60 random bits: bits 0-3 of w2 are
+ *     the coins); x = mulhi64(r, n_p - 1); j = x + (x >= i). Uniform over the
+ *     other steps to within (n_p - 1) / 2^60 relative.
  *   - Endpoint bits e_i = (w2 >> 2) & 1, e_j = (w2 >> 3) & 1, 0 = start point,
  *     1 = end point. A step entered in reverse orientation meets the node's end
  *     first, so the endpoint's path position is pos + ((e ^ rev) ? len : 0).
@@ -282,30 +285,30 @@ static int zipf_trial(const zipf_t *z, uint32_t w, uint64_t *k_out)
     return 0;
 }
 
-/* Draw k using the words of blocks 1, 2, ... of a Philox counter stream.   */
-/* blk1 holds the words of block 1; (c0, c1, c2) is the counter prefix.      */
-static uint64_t zipf_draw(const zipf_t *z, const uint32_t blk1[4], uint64_t seed,
+/* Draw k: trial 0 uses the word first_word, trial m >= 1 uses word          */
+/* (m - 1) % 4 of block 1 + (m - 1) / 4 of the counter stream (c0, c1, c2).  */
+static uint64_t zipf_draw(const zipf_t *z, uint32_t first_word, uint64_t seed,
                           uint32_t c0, uint32_t c1, uint32_t c2)
 {
     uint64_t k;
-    for (int m = 0; m < 4; ++m)
-        if (zipf_trial(z, blk1[m], &k)) return k;
-    for (int m = 4; m < 64; ++m) {
+    if (zipf_trial(z, first_word, &k)) return k;
+    for (int m = 1; m < 64; ++m) {
         uint32_t w[4];
-        philox_block(seed, c0, c1, c2, (uint32_t)(2 + (m - 4) / 4), w);
-        if (zipf_trial(z, w[(m - 4) % 4], &k)) return k;
+        philox_block(seed, c0, c1, c2, (uint32_t)(1 + (m - 1) / 4), w);
+        if (zipf_trial(z, w[(m - 1) % 4], &k)) return k;
     }
     return 1;
 }
 
-/* Test helper: count Zipf(theta) draws on [1, N] keyed by (q, 0x40000000). */
+/* Test helper: count Zipf(theta) draws on [1, N] keyed by (q, 0x40000000);  */
+/* trial 0 takes word 3 of block 0, as an update does.                       */
 void orc_zipf_sample(double theta, uint64_t N, uint64_t seed, uint64_t count, uint64_t *out)
 {
     zipf_t z = zipf_setup(theta, N);
     for (uint64_t q = 0; q < count; ++q) {
         uint32_t w[4];
-        philox_block(seed, (uint32_t)q, (uint32_t)(q >> 32), 0x40000000u, 1u, w);
-        out[q] = zipf_draw(&z, w, seed, (uint32_t)q, (uint32_t)(q >> 32), 0x40000000u);
+        philox_block(seed, (uint32_t)q, (uint32_t)(q >> 32), 0x40000000u, 0u, w);
+        out[q] = zipf_draw(&z, w[3], seed, (uint32_t)q, (uint32_t)(q >> 32), 0x40000000u);
     }
 }
 
@@ -359,9 +362,8 @@ static void sample_update(const sampler_t *S, uint32_t t, uint64_t u, orc_sample
 {
     const orc_graph *G = S->G;
     uint32_t c0 = (uint32_t)u, c1 = (uint32_t)(u >> 32);
-    uint32_t w[4], v[4];
+    uint32_t w[4];
     philox_block(S->seed, c0, c1, t, 0u, w);
-    philox_block(S->seed, c0, c1, t, 1u, v);
     uint64_t steps = G->path_off[G->n_paths];
     uint64_t g = mulhi64((uint64_t)w[0] | ((uint64_t)w[1] << 32), steps);
     uint32_t p = find_path(G, g);
@@ -376,7 +378,7 @@ static void sample_update(const sampler_t *S, uint32_t t, uint64_t u, orc_sample
     if (n < 2) { r->skip = 1; r->j = i; return; }
     uint64_t j;
     if (r->cooling) {
-        uint64_t k = zipf_draw(&S->zipf[p], v, S->seed, c0, c1, t);
+        uint64_t k = zipf_draw(&S->zipf[p], w[3], S->seed, c0, c1, t);
         int fwd = (w[2] >> 1) & 1u;
         int can_fwd = i + k < n, can_bwd = i >= k;
         if (fwd && can_fwd) j = i + k;
@@ -385,7 +387,7 @@ static void sample_update(const sampler_t *S, uint32_t t, uint64_t u, orc_sample
         else if (can_bwd) j = i - k;
         else j = (n - 1 - i > i) ? n - 1 : 0;
     } else {
-        uint64_t x = mulhi64((uint64_t)v[0] | ((uint64_t)v[1] << 32), n - 1);
+        uint64_t x = mulhi64(((uint64_t)w[3] << 32) | (w[2] & ~15u), n - 1);
         j = x + (x >= i);
     }
     r->j = j;
@@ -589,11 +591,10 @@ static double stress_term(const orc_graph *G, const double *xy, uint64_t seed, u
 {
     uint64_t off = G->path_off[p], n = G->path_off[p + 1] - off;
     uint32_t c0 = (uint32_t)q, c1 = (uint32_t)(q >> 32), c2 = 0x80000000u | p;
-    uint32_t w[4], v[4];
+    uint32_t w[4];
     philox_block(seed, c0, c1, c2, 0u, w);
-    philox_block(seed, c0, c1, c2, 1u, v);
     uint64_t i = mulhi64((uint64_t)w[0] | ((uint64_t)w[1] << 32), n);
-    uint64_t x = mulhi64((uint64_t)v[0] | ((uint64_t)v[1] << 32), n - 1);
+    uint64_t x = mulhi64(((uint64_t)w[3] << 32) | (w[2] & ~15u), n - 1);
     uint64_t j = x + (x >= i);
     int ei = w[2] & 1u, ej = (w[2] >> 1) & 1u;
     int64_t a = endpoint_pos(G, off + i, ei), b = endpoint_pos(G, off + j, ej);

@@ -93,13 +93,17 @@ def test_sampled_stress_tracks_full_stress_across_layouts():
 
 
 def test_sampled_stress_stable_across_sampling_seeds():
+    # Section VI-B: consistent across sampling seeds for one layout. The terms
+    # are heavy-tailed (a rare tiny-d_ref pair can dominate a sample set), so
+    # consistency is stated as pairwise overlap of the 95 % intervals.
     g = make_graph("tiny")
     xy, _ = O.layout(g, g.init_xy, seed=1)
-    vals = [O.sampled_stress(g, xy, seed=s) for s in range(5)]
-    m = np.array([v["mean"] for v in vals])
-    for v in vals:
-        # every estimate sits inside the others' confidence intervals' span
-        assert v["ci_lo"] <= m.mean() <= v["ci_hi"] or abs(v["mean"] - m.mean()) < 4 * (v["ci_hi"] - v["ci_lo"])
+    vals = [O.sampled_stress(g, xy, seed=s) for s in range(8)]
+    for a in vals:
+        for b in vals:
+            assert a["ci_lo"] <= b["ci_hi"] and b["ci_lo"] <= a["ci_hi"]
+    med = np.median([v["mean"] for v in vals])
+    assert sum(v["ci_lo"] <= med <= v["ci_hi"] for v in vals) >= 6
 
 
 def test_threaded_stress_matches_sequential():
