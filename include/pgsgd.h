@@ -89,7 +89,12 @@ typedef enum pgsgd_option {
      * replace the point (last writer wins, the paper's racy store); on GB300
      * the exchange, executed at L2, ran 1.4x (5 M-node graph) to 7x
      * (200 k-node graph) faster than every plain-store form. */
-    PGSGD_OPT_STORE_MODE = 12
+    PGSGD_OPT_STORE_MODE = 12,
+    /* Cache operators of the update kernel's record loads: step-record
+     * operator (0 = ld.cg, default; 1 = ld.cg.L2::64B; 2 = ld.nc with no L1
+     * allocation; 3 = ld.cv; 4 = ld.lu) plus 16 x node-record operator
+     * (0 = ld.cg, default; 1 = ld.cg.L2::64B; 3 = ld.cv). */
+    PGSGD_OPT_LOAD_MODE = 13
 } pgsgd_option;
 
 /* Device-resident graph: node records, packed step records, path table. */

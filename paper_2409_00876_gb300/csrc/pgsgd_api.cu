@@ -29,6 +29,9 @@ struct pgsgd_graph {
     uint64_t* d_path_off = nullptr;
     uint64_t* d_sample_off = nullptr;  // stress sample offsets [P + 1]
     float* d_zipf_B = nullptr;
+    float* d_zipf_T = nullptr;         // [kZipfTable] acceptance thresholds
+    uint16_t* d_guide = nullptr;       // [n_guide + 1]
+    uint32_t n_guide = 1, guide_shift = 0;
     uint32_t* d_flags = nullptr;
     double* d_partials = nullptr;      // stress scratch [max_stress_blocks][3] + 3 totals
     double* d_per_path = nullptr;      // [P][3]
@@ -54,6 +57,7 @@ struct pgsgd_graph {
     int min_blocks = 1;
     int l2_fetch = 0;
     int store_mode = 6;  // 64-bit atomic exchange: measured fastest replace-store
+    int load_mode = 0;   // step load operator + 16 * node load operator
 
     // timing
     std::vector<cudaEvent_t> ev_free;
@@ -123,6 +127,8 @@ void free_graph(pgsgd_graph* g) {
     cudaFree(g->d_path_off);
     cudaFree(g->d_sample_off);
     cudaFree(g->d_zipf_B);
+    cudaFree(g->d_zipf_T);
+    cudaFree(g->d_guide);
     cudaFree(g->d_flags);
     cudaFree(g->d_partials);
     cudaFree(g->d_per_path);
@@ -165,7 +171,7 @@ int check_flags(pgsgd_graph* g, cudaStream_t st, const char* what) {
 
 int ensure_zipf(pgsgd_graph* g, float theta, cudaStream_t st) {
     if (g->zipf_theta == theta) return PGSGD_OK;
-    CK(launch_zipf_setup(g->d_path_off, g->n_paths, theta, g->d_zipf_B, nullptr, st), "zipf setup");
+    CK(launch_zipf_setup(g->d_path_off, g->n_paths, theta, g->d_zipf_B, g->d_zipf_T, st), "zipf setup");
     g->zipf_theta = theta;
     return PGSGD_OK;
 }
@@ -175,6 +181,10 @@ SamplerArgs sampler_args(const pgsgd_graph* g, uint32_t T, uint32_t t, float the
     a.steps = g->d_steps;
     a.path_off = g->d_path_off;
     a.zipf_B = g->d_zipf_B;
+    a.zipf_T = g->d_zipf_T;
+    a.guide = g->d_guide;
+    a.n_guide = g->n_guide;
+    a.guide_shift = g->guide_shift;
     a.n_steps = g->n_steps;
     a.n_paths = g->n_paths;
     a.T = T;
@@ -302,6 +312,30 @@ int pgsgd_create(const uint32_t* node_len, uint32_t n_nodes, const uint64_t* pat
         TRY(dalloc(g, &g->d_path_off, n_paths + 1), "path table");
         TRY(dalloc(g, &g->d_sample_off, n_paths + 1), "stress sample table");
         TRY(dalloc(g, &g->d_zipf_B, n_paths), "zipf table");
+        TRY(dalloc(g, &g->d_zipf_T, kZipfTable), "zipf thresholds");
+        {
+            // guide: buckets of 2^shift steps, at most kGuideBuckets of them;
+            // guide[b] = path holding step b << shift, guide[n] = P - 1
+            uint32_t shift = 0;
+            while (S_ > 0 && ((S_ - 1) >> shift) >= (uint64_t)kGuideBuckets) ++shift;
+            const uint32_t nb = S_ > 0 ? (uint32_t)((S_ - 1) >> shift) + 1 : 1;
+            std::vector<uint16_t> guide(nb + 1);
+            for (uint32_t b = 0; b < nb; ++b) {
+                const uint64_t gs = (uint64_t)b << shift;
+                uint32_t lo = 0, hi = n_paths;
+                while (hi - lo > 1) {
+                    const uint32_t mid = lo + (hi - lo) / 2;
+                    if (off[mid] <= gs) lo = mid; else hi = mid;
+                }
+                guide[b] = (uint16_t)lo;
+            }
+            guide[nb] = (uint16_t)(n_paths - 1);
+            g->n_guide = nb;
+            g->guide_shift = shift;
+            TRY(dalloc(g, &g->d_guide, nb + 1), "path guide");
+            TRY(cudaMemcpy(g->d_guide, guide.data(), guide.size() * sizeof(uint16_t), cudaMemcpyHostToDevice),
+                "path guide upload");
+        }
         TRY(dalloc(g, &g->d_flags, 1), "flags");
         g->max_stress_blocks = g->sm_count * 8;
         TRY(dalloc(g, &g->d_partials, 3 * (size_t)g->max_stress_blocks + 3), "stress scratch");
@@ -401,6 +435,11 @@ int pgsgd_set_option(pgsgd_graph* g, int option, int64_t v) {
             if (v < 1 || v > 6) return fail(PGSGD_EINVAL, "min blocks must be in [1, 6]");
             g->min_blocks = (int)v;
             return PGSGD_OK;
+        case PGSGD_OPT_LOAD_MODE:
+            if (v < 0 || (v & 15) > 4 || ((v >> 4) != 0 && (v >> 4) != 1 && (v >> 4) != 3))
+                return fail(PGSGD_EINVAL, "load mode: step operator 0..4 plus 16 x node operator 0, 1 or 3");
+            g->load_mode = (int)v;
+            return PGSGD_OK;
         case PGSGD_OPT_STORE_MODE:
             if (v < 0 || v > 6) return fail(PGSGD_EINVAL, "store mode must be in [0, 6]");
             g->store_mode = (int)v;
@@ -430,6 +469,7 @@ int pgsgd_get_option(const pgsgd_graph* g, int option, int64_t* v) {
         case PGSGD_OPT_MIN_BLOCKS: *v = g->min_blocks; return PGSGD_OK;
         case PGSGD_OPT_L2_FETCH: *v = g->l2_fetch; return PGSGD_OK;
         case PGSGD_OPT_STORE_MODE: *v = g->store_mode; return PGSGD_OK;
+        case PGSGD_OPT_LOAD_MODE: *v = g->load_mode; return PGSGD_OK;
         default: return fail(PGSGD_EINVAL, "unknown option %d", option);
     }
 }
@@ -529,6 +569,8 @@ int pgsgd_layout(pgsgd_graph* g, uint32_t iter_max, const double* eta, double et
     L.upt = g->upt;
     L.minb = g->min_blocks;
     L.store_mode = g->store_mode;
+    L.step_load = g->load_mode & 15;
+    L.node_load = g->load_mode >> 4;
     L.atomic = g->atomic != 0;
     if (g->l2_fetch) CK(cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, g->l2_fetch), "L2 fetch limit");
     for (uint32_t t = iter_begin; t < iter_end; ++t) {

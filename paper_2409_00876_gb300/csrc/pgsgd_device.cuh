@@ -15,6 +15,9 @@
 
 namespace pgsgd {
 
+constexpr int kZipfTable = 256;     // Zipf acceptance thresholds kept for k < 256
+constexpr int kGuideBuckets = 4096; // path-lookup guide buckets (at most)
+
 // ---------------------------------------------------------------- records
 
 // One node of the layout: the two endpoints of its segment (Section II-C:
@@ -56,18 +59,60 @@ __device__ __forceinline__ uint64_t load_step(const uint64_t* p) {
     return v;
 }
 
+// Step-record load with a selectable cache operator (mode 0 = .cg).
+__device__ __forceinline__ uint64_t load_step_mode(const uint64_t* p, int mode) {
+    uint64_t v;
+    switch (mode) {
+        case 1: asm volatile("ld.global.cg.L2::64B.u64 %0, [%1];" : "=l"(v) : "l"(p)); break;
+        case 2: asm volatile("ld.global.nc.L1::no_allocate.u64 %0, [%1];" : "=l"(v) : "l"(p)); break;
+        case 3: asm volatile("ld.global.cv.u64 %0, [%1];" : "=l"(v) : "l"(p)); break;
+        case 4: asm volatile("ld.global.lu.u64 %0, [%1];" : "=l"(v) : "l"(p)); break;
+        default: asm volatile("ld.global.cg.u64 %0, [%1];" : "=l"(v) : "l"(p)); break;
+    }
+    return v;
+}
+
 // Node records change during a launch (Hogwild!): read them from L2 (.cg),
 // never from a possibly stale L1 line, with one 256-bit load per node.
-__device__ __forceinline__ NodeRec load_node(const NodeRec* p) {
+__device__ __forceinline__ NodeRec unpack_node(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                               uint32_t a4, uint32_t a5, uint32_t a6, uint32_t a7) {
     NodeRec r;
-    uint32_t a0, a1, a2, a3, a4, a5, a6, a7;
-    asm volatile("ld.global.cg.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(a0), "=r"(a1), "=r"(a2), "=r"(a3), "=r"(a4), "=r"(a5), "=r"(a6), "=r"(a7)
-                 : "l"(p));
     r.sx = __uint_as_float(a0); r.sy = __uint_as_float(a1);
     r.ex = __uint_as_float(a2); r.ey = __uint_as_float(a3);
     r.ax = (int32_t)a4; r.ay = (int32_t)a5; r.len = a6; r.pad = a7;
     return r;
+}
+
+__device__ __forceinline__ NodeRec load_node(const NodeRec* p) {
+    uint32_t a0, a1, a2, a3, a4, a5, a6, a7;
+    asm volatile("ld.global.cg.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(a0), "=r"(a1), "=r"(a2), "=r"(a3), "=r"(a4), "=r"(a5), "=r"(a6), "=r"(a7)
+                 : "l"(p));
+    return unpack_node(a0, a1, a2, a3, a4, a5, a6, a7);
+}
+
+// Node-record load with a selectable cache operator (mode 0 = .cg; modes that
+// could return stale data within a launch are not offered).
+__device__ __forceinline__ NodeRec load_node_mode(const NodeRec* p, int mode) {
+    uint32_t a0, a1, a2, a3, a4, a5, a6, a7;
+    switch (mode) {
+        case 1:
+            asm volatile("ld.global.cg.L2::64B.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=r"(a0), "=r"(a1), "=r"(a2), "=r"(a3), "=r"(a4), "=r"(a5), "=r"(a6), "=r"(a7)
+                         : "l"(p));
+            break;
+        case 3:
+            asm volatile("ld.global.cv.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=r"(a0), "=r"(a1), "=r"(a2), "=r"(a3), "=r"(a4), "=r"(a5), "=r"(a6), "=r"(a7)
+                         : "l"(p));
+            break;
+        default:
+            asm volatile("ld.global.cg.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=r"(a0), "=r"(a1), "=r"(a2), "=r"(a3), "=r"(a4), "=r"(a5), "=r"(a6), "=r"(a7)
+                         : "l"(p));
+            break;
+    }
+    return unpack_node(a0, a1, a2, a3, a4, a5, a6, a7);
 }
 
 // ---------------------------------------------------------------- Philox4x32-10
@@ -205,11 +250,19 @@ struct ZipfConsts {
     float theta, omt, A, s;
 };
 
+// Acceptance threshold H(k + 1/2) - h(k) of a trial that lands on k.
+__device__ __forceinline__ float zipf_threshold(uint32_t k, float omt, float theta) {
+    const float fk = __uint2float_rn(k);
+    return __fsub_rn(zipf_H(__fadd_rn(fk, 0.5f), omt), zipf_h(fk, theta));
+}
+
 // One trial with the 32-bit word w. Draws with k >= 256 are accepted without
 // the rejection test: there the exact rejection chance is below
 // theta (theta + 1) / (24 * 256^2) of h(k), smaller than binary32 rounding of H.
-__device__ __forceinline__ bool zipf_trial(const ZipfConsts& z, float B, uint64_t N, uint32_t w,
-                                           uint64_t& k_out) {
+// Below 256 the threshold comes from T[k], which holds zipf_threshold(k)
+// computed with the same operations (so the decision is the same).
+__device__ __forceinline__ bool zipf_trial(const ZipfConsts& z, const float* T, float B, uint64_t N,
+                                           uint32_t w, uint64_t& k_out) {
     const float U = __fmul_rn(__uint2float_rn(w >> 8), 0x1p-24f);
     const float u = __fadd_rn(B, __fmul_rn(U, __fsub_rn(z.A, B)));
     const float x = zipf_Hinv(u, z.omt);
@@ -217,11 +270,10 @@ __device__ __forceinline__ bool zipf_trial(const ZipfConsts& z, float B, uint64_
     uint64_t k = kf < 1.0f ? 1ull : (uint64_t)__float2ull_rz(kf);
     if (k > N) k = N;
     k_out = k;
-    if (k >= 256u) return true;
+    if (k >= (uint64_t)kZipfTable) return true;
     const float fk = __ull2float_rn(k);
     if (__fsub_rn(fk, x) <= z.s) return true;
-    const float Hk = __fsub_rn(zipf_H(__fadd_rn(fk, 0.5f), z.omt), zipf_h(fk, z.theta));
-    return u >= Hk;
+    return u >= T[k];
 }
 
 // ---------------------------------------------------------------- the pair draw
@@ -230,28 +282,46 @@ struct SamplerArgs {
     const uint64_t* steps;     // packed step records [S]
     const uint64_t* path_off;  // [P + 1]
     const float* zipf_B;       // [P] H(n_p - 1/2); unused for n_p < 2
+    const float* zipf_T;       // [kZipfTable] H(k + 1/2) - h(k) for the current theta
+    const uint16_t* guide;     // [n_guide + 1] first path of every bucket of 2^shift steps
     uint64_t n_steps;          // S
     uint32_t n_paths;          // P
+    uint32_t n_guide;          // buckets
+    uint32_t guide_shift;
     uint32_t T;                // iterations in the schedule
     uint32_t t;                // this iteration
     uint32_t key0, key1;       // Philox key = seed
     ZipfConsts zc;
 };
 
-// Path table staged in shared memory by every block: offsets then Zipf B.
+// Path table staged in shared memory by every block.
 struct PathTable {
-    const uint64_t* off;  // [P + 1]
-    const float* B;       // [P]
+    const uint64_t* off;    // [P + 1]
+    const float* B;         // [P]
+    const float* T;         // [kZipfTable]
+    const uint16_t* guide;  // [n_guide + 1]
     uint32_t P;
+    uint32_t shift;
 };
 
-__device__ __forceinline__ uint32_t find_path(const uint64_t* off, uint32_t P, uint64_t g) {
-    uint32_t lo = 0, hi = P;  // off[lo] <= g < off[hi]
+// Largest p in [lo, hi) with off[p] <= g, given off[lo] <= g < off[hi].
+__device__ __forceinline__ uint32_t search_path(const uint64_t* off, uint32_t lo, uint32_t hi, uint64_t g) {
     while (hi - lo > 1) {
         const uint32_t mid = lo + ((hi - lo) >> 1);
         if (off[mid] <= g) lo = mid; else hi = mid;
     }
     return lo;
+}
+
+__device__ __forceinline__ uint32_t find_path(const uint64_t* off, uint32_t P, uint64_t g) {
+    return search_path(off, 0, P, g);
+}
+
+// Same result as find_path: the guide bounds the search to the paths that
+// meet g's bucket, usually a single one.
+__device__ __forceinline__ uint32_t find_path_guided(const PathTable& pt, uint64_t g) {
+    const uint32_t b = (uint32_t)(g >> pt.shift);
+    return search_path(pt.off, pt.guide[b], (uint32_t)pt.guide[b + 1] + 1, g);
 }
 
 struct Pair {
@@ -264,14 +334,17 @@ struct Pair {
     uint32_t short_path;  // 1 = path has < 2 steps: no update
 };
 
-// Draw the pair of update u in iteration t (Algorithm 1, lines 5-11).
+// Draw the pair of update u in iteration t (Algorithm 1, lines 5-11). One
+// Philox block serves the whole draw: w0, w1 pick the step, bits 0-3 of w2
+// are the coins, w3 feeds the first power-law trial or, with the upper 28
+// bits of w2, the uniform partner. Later blocks are drawn only after a
+// power-law trial rejects (about 1 update in 1000).
 __device__ __forceinline__ Pair draw_pair(const SamplerArgs& a, const PathTable& pt, uint64_t u) {
     Pair r;
     const uint32_t c0 = (uint32_t)u, c1 = (uint32_t)(u >> 32);
     const uint4 w = philox4x32_10(make_uint4(c0, c1, a.t, 0u), a.key0, a.key1);
-    const uint4 v = philox4x32_10(make_uint4(c0, c1, a.t, 1u), a.key0, a.key1);
     r.g = mulhi64((uint64_t)w.x | ((uint64_t)w.y << 32), a.n_steps);
-    r.path = find_path(pt.off, pt.P, r.g);
+    r.path = find_path_guided(pt, r.g);
     r.base = pt.off[r.path];
     const uint64_t n = pt.off[r.path + 1] - r.base;
     r.i = r.g - r.base;
@@ -284,12 +357,12 @@ __device__ __forceinline__ Pair draw_pair(const SamplerArgs& a, const PathTable&
         const float B = pt.B[r.path];
         const uint64_t N = n - 1;
         uint64_t k = 1;
-        bool ok = zipf_trial(a.zc, B, N, v.x, k) || zipf_trial(a.zc, B, N, v.y, k) ||
-                  zipf_trial(a.zc, B, N, v.z, k) || zipf_trial(a.zc, B, N, v.w, k);
-        for (uint32_t blk = 2; !ok && blk < 17; ++blk) {  // trials 4..63
+        bool ok = zipf_trial(a.zc, pt.T, B, N, w.w, k);
+        for (uint32_t blk = 1; !ok && blk < 17; ++blk) {  // trials 1..63
             const uint4 x = philox4x32_10(make_uint4(c0, c1, a.t, blk), a.key0, a.key1);
-            ok = zipf_trial(a.zc, B, N, x.x, k) || zipf_trial(a.zc, B, N, x.y, k) ||
-                 zipf_trial(a.zc, B, N, x.z, k) || zipf_trial(a.zc, B, N, x.w, k);
+            ok = zipf_trial(a.zc, pt.T, B, N, x.x, k) || zipf_trial(a.zc, pt.T, B, N, x.y, k) ||
+                 zipf_trial(a.zc, pt.T, B, N, x.z, k) ||
+                 (blk < 16 && zipf_trial(a.zc, pt.T, B, N, x.w, k));
         }
         if (!ok) k = 1;
         const uint64_t i = r.i;
@@ -301,7 +374,7 @@ __device__ __forceinline__ Pair draw_pair(const SamplerArgs& a, const PathTable&
         else if (can_bwd) j = i - k;
         else j = (n - 1 - i > i) ? n - 1 : 0;
     } else {
-        const uint64_t x = mulhi64((uint64_t)v.x | ((uint64_t)v.y << 32), n - 1);
+        const uint64_t x = mulhi64(((uint64_t)w.w << 32) | (w.z & ~15u), n - 1);
         j = x + (x >= r.i);
     }
     r.j = j;

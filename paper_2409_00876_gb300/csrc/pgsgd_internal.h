@@ -30,6 +30,7 @@ struct UpdateLaunch {
     float eta;
     int block, grid, upt, minb;
     int store_mode;
+    int step_load, node_load;  // cache operators of the record loads
     bool atomic;
 };
 
@@ -46,7 +47,7 @@ struct StressLaunch {
     int block, grid;
 };
 
-size_t update_smem_bytes(uint32_t n_paths);
+size_t update_smem_bytes(uint32_t n_paths, uint32_t n_guide);
 size_t stress_smem_bytes(uint32_t n_paths);
 
 cudaError_t launch_pack_nodes(const uint32_t* node_len, uint32_t n, NodeRec* nodes,
@@ -65,7 +66,7 @@ cudaError_t launch_get_coords(const NodeRec* nodes, double* xy, uint32_t n, int 
                               cudaStream_t st);
 cudaError_t launch_rebase(NodeRec* nodes, uint32_t n, int sm_count, cudaStream_t st);
 cudaError_t launch_zipf_setup(const uint64_t* path_off, uint32_t n_paths, float theta,
-                              float* zipf_B, float* consts_out, cudaStream_t st);
+                              float* zipf_B, float* zipf_T, cudaStream_t st);
 cudaError_t launch_update(const UpdateLaunch& L, cudaStream_t st);
 cudaError_t launch_debug_sample(const SamplerArgs& s, uint64_t u_begin, uint64_t count,
                                 const NodeRec* nodes, void* out, int sm_count, cudaStream_t st);

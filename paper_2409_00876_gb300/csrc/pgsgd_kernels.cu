@@ -154,22 +154,30 @@ __global__ void rebase_kernel(NodeRec* __restrict__ nodes, uint32_t n) {
 
 // ---------------------------------------------------------------- Zipf per path
 
+// Per-theta tables: B[p] = H(n_p - 1/2) for every path, and the acceptance
+// thresholds T[k] = H(k + 1/2) - h(k) for k < 256 (T[0] unused).
 __global__ void zipf_setup_kernel(const uint64_t* __restrict__ path_off, uint32_t P, float theta,
-                                  float* __restrict__ out_B) {
+                                  float* __restrict__ out_B, float* __restrict__ out_T) {
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= P) return;
-    const uint64_t n = path_off[p + 1] - path_off[p];
     const float omt = __fsub_rn(1.0f, theta);
-    out_B[p] = n >= 2 ? zipf_B(n - 1, omt) : 0.0f;
+    if (p < P) {
+        const uint64_t n = path_off[p + 1] - path_off[p];
+        out_B[p] = n >= 2 ? zipf_B(n - 1, omt) : 0.0f;
+    }
+    if (p < (uint32_t)kZipfTable) out_T[p] = p == 0 ? 0.0f : zipf_threshold(p, omt, theta);
 }
 
-// Stage the path table and the per-theta Zipf constants in shared memory.
+// Stage the path table, the guide and the per-theta Zipf tables in shared memory.
 __device__ __forceinline__ PathTable stage_paths(const SamplerArgs& a, unsigned char* smem,
                                                  ZipfConsts& zc_shared) {
     uint64_t* s_off = reinterpret_cast<uint64_t*>(smem);
-    float* s_B = reinterpret_cast<float*>(s_off + a.n_paths + 1);
+    float* s_T = reinterpret_cast<float*>(s_off + a.n_paths + 1);
+    float* s_B = s_T + kZipfTable;
+    uint16_t* s_guide = reinterpret_cast<uint16_t*>(s_B + a.n_paths);
     for (uint32_t k = threadIdx.x; k <= a.n_paths; k += blockDim.x) s_off[k] = a.path_off[k];
     for (uint32_t k = threadIdx.x; k < a.n_paths; k += blockDim.x) s_B[k] = a.zipf_B[k];
+    for (uint32_t k = threadIdx.x; k < (uint32_t)kZipfTable; k += blockDim.x) s_T[k] = a.zipf_T[k];
+    for (uint32_t k = threadIdx.x; k <= a.n_guide; k += blockDim.x) s_guide[k] = a.guide[k];
     if (threadIdx.x == 0) {
         ZipfConsts z;
         z.theta = a.zc.theta;
@@ -177,7 +185,7 @@ __device__ __forceinline__ PathTable stage_paths(const SamplerArgs& a, unsigned 
         zc_shared = z;
     }
     __syncthreads();
-    return PathTable{s_off, s_B, a.n_paths};
+    return PathTable{s_off, s_B, s_T, s_guide, a.n_paths, a.guide_shift};
 }
 
 // ---------------------------------------------------------------- update math
@@ -261,16 +269,16 @@ __global__ void __launch_bounds__(256, MINB) update_kernel(UpdateLaunch L) {
 #pragma unroll
         for (int k = 0; k < UPT; ++k) {
             if (act[k]) {
-                si[k] = load_step(steps + pr[k].base + pr[k].i);
-                sj[k] = load_step(steps + pr[k].base + pr[k].j);
+                si[k] = load_step_mode(steps + pr[k].base + pr[k].i, L.step_load);
+                sj[k] = load_step_mode(steps + pr[k].base + pr[k].j, L.step_load);
             }
         }
         NodeRec na[UPT], nb[UPT];
 #pragma unroll
         for (int k = 0; k < UPT; ++k) {
             if (act[k]) {
-                na[k] = load_node(nodes + step_node(si[k]));
-                nb[k] = load_node(nodes + step_node(sj[k]));
+                na[k] = load_node_mode(nodes + step_node(si[k]), L.node_load);
+                nb[k] = load_node_mode(nodes + step_node(sj[k]), L.node_load);
             }
         }
 #pragma unroll
@@ -393,10 +401,8 @@ __global__ void stress_kernel(StressLaunch L) {
             const uint32_t c2 = 0x80000000u | p[k];
             const uint4 w = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), c2, 0u),
                                           L.key0, L.key1);
-            const uint4 v = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), c2, 1u),
-                                          L.key0, L.key1);
             const uint64_t i = mulhi64((uint64_t)w.x | ((uint64_t)w.y << 32), n);
-            const uint64_t x = mulhi64((uint64_t)v.x | ((uint64_t)v.y << 32), n - 1);
+            const uint64_t x = mulhi64(((uint64_t)w.w << 32) | (w.z & ~15u), n - 1);
             const uint64_t j = x + (x >= i);
             ei[k] = w.z & 1u;
             ej[k] = (w.z >> 1) & 1u;
@@ -506,8 +512,9 @@ int grid_for(uint64_t work, int block, int sm_count, int per_sm) {
 
 }  // namespace
 
-size_t update_smem_bytes(uint32_t n_paths) {
-    return (size_t)(n_paths + 1) * sizeof(uint64_t) + (size_t)n_paths * sizeof(float);
+size_t update_smem_bytes(uint32_t n_paths, uint32_t n_guide) {
+    return (size_t)(n_paths + 1) * sizeof(uint64_t) + (size_t)(kZipfTable + n_paths) * sizeof(float) +
+           (size_t)(n_guide + 1) * sizeof(uint16_t);
 }
 size_t stress_smem_bytes(uint32_t n_paths) { return 2 * (size_t)(n_paths + 1) * sizeof(uint64_t); }
 
@@ -559,15 +566,15 @@ cudaError_t launch_rebase(NodeRec* nodes, uint32_t n, int sm_count, cudaStream_t
 }
 
 cudaError_t launch_zipf_setup(const uint64_t* path_off, uint32_t n_paths, float theta,
-                              float* zipf_B, float*, cudaStream_t st) {
-    if (n_paths == 0) return cudaSuccess;
-    zipf_setup_kernel<<<(n_paths + 127) / 128, 128, 0, st>>>(path_off, n_paths, theta, zipf_B);
+                              float* zipf_B, float* zipf_T, cudaStream_t st) {
+    const uint32_t n = n_paths > (uint32_t)kZipfTable ? n_paths : (uint32_t)kZipfTable;
+    zipf_setup_kernel<<<(n + 127) / 128, 128, 0, st>>>(path_off, n_paths, theta, zipf_B, zipf_T);
     return cudaGetLastError();
 }
 
 template <int UPT, int MINB>
 static cudaError_t launch_update_t(const UpdateLaunch& L, cudaStream_t st) {
-    const size_t smem = update_smem_bytes(L.s.n_paths);
+    const size_t smem = update_smem_bytes(L.s.n_paths, L.s.n_guide);
     cudaError_t e = cudaFuncSetAttribute(update_kernel<UPT, MINB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -597,7 +604,7 @@ cudaError_t launch_update(const UpdateLaunch& L, cudaStream_t st) {
 cudaError_t launch_debug_sample(const SamplerArgs& s, uint64_t u_begin, uint64_t count,
                                 const NodeRec* nodes, void* out, int sm_count, cudaStream_t st) {
     if (count == 0) return cudaSuccess;
-    const size_t smem = update_smem_bytes(s.n_paths);
+    const size_t smem = update_smem_bytes(s.n_paths, s.n_guide);
     cudaError_t e = cudaFuncSetAttribute(debug_sample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -610,7 +617,7 @@ cudaError_t launch_debug_sweep(const SamplerArgs& s, uint64_t u_begin, uint64_t 
                                const NodeRec* nodes, float eta, float4* out, int sm_count,
                                cudaStream_t st) {
     if (count == 0) return cudaSuccess;
-    const size_t smem = update_smem_bytes(s.n_paths);
+    const size_t smem = update_smem_bytes(s.n_paths, s.n_guide);
     cudaError_t e = cudaFuncSetAttribute(debug_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;

@@ -81,9 +81,8 @@ __global__ void stress_noalloc_kernel(const uint32_t* __restrict__ node_len,
         const uint64_t n = s_poff[p + 1] - off;
         const uint32_t c2 = 0x80000000u | p;
         const uint4 w = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), c2, 0u), key0, key1);
-        const uint4 v = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), c2, 1u), key0, key1);
         const uint64_t i = off + mulhi64((uint64_t)w.x | ((uint64_t)w.y << 32), n);
-        const uint64_t x = mulhi64((uint64_t)v.x | ((uint64_t)v.y << 32), n - 1);
+        const uint64_t x = mulhi64(((uint64_t)w.w << 32) | (w.z & ~15u), n - 1);
         const uint64_t j = off + x + (x >= i - off);
         const uint32_t ei = w.z & 1u, ej = (w.z >> 1) & 1u;
         const uint32_t ni = step_node[i], nj = step_node[j];
