@@ -279,18 +279,19 @@ def run_gpu(args):
     total_updates = sum_over_ranks(updates_per_step * args.steps, dev)
     value = total_updates / (ms_max / 1e3)
 
-    # kernels launched per step: set_coords, 30 x (update + rebase), stress + finalize
-    gpu_launches = args.steps * (1 + 2 * ITERS + 2)
+    # kernels launched per step: set_coords + anchor refresh, 30 x (update +
+    # rebase + anchor refresh), stress + finalize
+    gpu_launches = args.steps * (2 + 3 * ITERS + 2)
     peak, peak_kind = peaks()
     per_launch_ms = upd_ms / max(launches, 1)
     updates_per_launch = upd / max(launches, 1)
     achieved = BYTES_PER_UPDATE * updates_per_launch / (per_launch_ms / 1e3) / 1e9
     traffic = None
-    tpath = os.path.join(ROOT, "profiles", "update_kernel_traffic.json")
+    tpath = os.path.join(ROOT, "profiles", f"update_kernel_traffic_{args.config}.json")
     if os.path.exists(tpath):
         tr = json.load(open(tpath))
-        if tr.get("config") == args.config and tr.get("kernel_rev") == kernel_revision():
-            traffic = tr["bytes_per_update"] * updates_per_launch
+        if tr.get("kernel_rev") == kernel_revision():
+            traffic = tr["dram_bytes_per_update"] * updates_per_launch
 
     # end to end through the public API with host buffers, copies inside the region
     e2e = run_e2e(pg, g, args, dev) if not args.skip_e2e else None

@@ -42,17 +42,19 @@ typedef enum pgsgd_status {
 
 /* Options for pgsgd_set_option / pgsgd_get_option. */
 typedef enum pgsgd_option {
-    /* Coordinate storage. 0 = anchored (default): a node whose coordinate on
-     * an axis is at least 4096 in magnitude keeps an integer anchor on that
-     * axis and FP32 offsets from it, so FP32 keeps sub-nucleotide resolution
-     * at chromosome scale (coordinates below 2^30).
-     * 1 = plain FP32 absolute coordinates. Takes effect at pgsgd_set_coords. */
+    /* Coordinate storage. 0 = anchored (default): a node whose start x is at
+     * least 4096 in magnitude keeps an integer x anchor and FP32 x offsets
+     * from it, so FP32 keeps sub-nucleotide resolution along a chromosome-
+     * scale layout (|x| < 2^30); y is plain FP32 (resolution better than
+     * 0.1 nt while |y| < 1e6). 1 = plain FP32 absolute coordinates. Takes
+     * effect at pgsgd_set_coords. */
     PGSGD_OPT_COORD_MODE = 1,
     /* Updates per iteration = this value times the number of path steps
      * (Algorithm 1, line 1 uses 10). Default 10. */
     PGSGD_OPT_UPDATES_PER_STEP = 2,
     /* Update-kernel launch shape: threads per block (64..256, multiple of
-     * 32; default 256), blocks per SM in the grid (default 8), and
+     * 32; default 256), blocks per SM in the grid (default 32: many short
+     * blocks let the block scheduler balance the two dies), and
      * updates each thread keeps in flight per loop trip (1, 2 or 4; default 2). */
     PGSGD_OPT_BLOCK = 3,
     PGSGD_OPT_BLOCKS_PER_SM = 4,
@@ -63,9 +65,10 @@ typedef enum pgsgd_option {
      * graphs under a full grid that diverges, so keep 0 unless the
      * concurrency cap makes collisions rare. */
     PGSGD_OPT_ATOMIC_UPDATES = 6,
-    /* 1 = after each iteration, move the anchor of every node whose start
+    /* 1 = after each iteration, move the x anchor of every node whose start
      * offset has drifted past 8 to the rounded start point, so the FP32
-     * offsets stay small (anchored mode; default 1). */
+     * offsets stay small, and copy the moved anchors into the step records
+     * (anchored mode; default 1). */
     PGSGD_OPT_REBASE = 7,
     /* 1 = record CUDA events around every update-kernel launch on the
      * launching stream; read them with pgsgd_timing_read. Default 0. */
@@ -84,17 +87,21 @@ typedef enum pgsgd_option {
      * default). Every access of the path is a random 32-byte sector. */
     PGSGD_OPT_L2_FETCH = 11,
     /* How a moved point is written when atomic updates are off: 0 = plain
-     * store, 1 = st.cg, 2 = st.cs, 3 = st.wt, 4 = st.relaxed.gpu,
-     * 5 = st.L1::no_allocate, 6 = 64-bit atomic exchange (default). All
-     * replace the point (last writer wins, the paper's racy store); on GB300
-     * the exchange, executed at L2, ran 1.4x (5 M-node graph) to 7x
-     * (200 k-node graph) faster than every plain-store form. */
+     * store, 1 = 64-bit atomic exchange (default). Both replace the point
+     * (last writer wins, the paper's racy store); on GB300 the exchange,
+     * executed at L2, ran 1.4x (5 M-node graph) to 7x (200 k-node graph)
+     * faster than every plain-store form (.wb, .cg, .cs, .wt, .relaxed.gpu,
+     * L1::no_allocate) in the earlier 32-byte node-record design. */
     PGSGD_OPT_STORE_MODE = 12,
-    /* Cache operators of the update kernel's record loads: step-record
-     * operator (0 = ld.cg, default; 1 = ld.cg.L2::64B; 2 = ld.nc with no L1
-     * allocation; 3 = ld.cv; 4 = ld.lu) plus 16 x node-record operator
-     * (0 = ld.cg, default; 1 = ld.cg.L2::64B; 3 = ld.cv). */
-    PGSGD_OPT_LOAD_MODE = 13
+    /* 1 (default) = L2 residency hints: step records are read evict-first,
+     * node records read and written evict-last, so the node array stays in
+     * L2 while the step records stream past. 0 = no hints. */
+    PGSGD_OPT_L2_HINTS = 13,
+    /* 64-byte L2 prefetch-size hint on the update kernel's record loads:
+     * bit 0 = step records, bit 1 = node records. Default 3 (both): without
+     * it a random 32-byte miss was promoted to 128 bytes, and the full
+     * chromosome layout ran at 14.4e9 instead of 18.6e9 updates/s. */
+    PGSGD_OPT_PREFETCH64 = 14
 } pgsgd_option;
 
 /* Device-resident graph: node records, packed step records, path table. */
@@ -170,8 +177,8 @@ int pgsgd_info_get(const pgsgd_graph *g, pgsgd_info *out);
 /*
  * Replace the layout (Algorithm 1, output L: one 2-D segment per node).
  * xy[n_nodes][4] float64 = (start x, start y, end x, end y), host or device.
- * Stored in FP32 (anchored mode: integer anchor + FP32 offset per axis,
- * which needs |coordinate| < 2^30; PGSGD_ERANGE otherwise). Queued on the
+ * Stored in FP32 (anchored mode: integer x anchor + FP32 x offset, which
+ * needs |x| < 2^30, PGSGD_ERANGE otherwise; y in plain FP32). Queued on the
  * stream; the caller's buffer may be reused when the call returns.
  */
 int pgsgd_set_coords(pgsgd_graph *g, const double *xy, int on_device, void *cuda_stream);

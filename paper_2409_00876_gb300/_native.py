@@ -18,7 +18,7 @@ PGSGD_OK, PGSGD_EINVAL, PGSGD_ERANGE, PGSGD_ENOMEM, PGSGD_ECUDA, PGSGD_ETIMEOUT,
 
 OPT = dict(coord_mode=1, updates_per_step=2, block=3, blocks_per_sm=4, updates_per_thread=5,
            atomic_updates=6, rebase=7, timing=8, max_concurrent=9,
-           min_blocks=10, l2_fetch=11, store_mode=12, load_mode=13)
+           min_blocks=10, l2_fetch=11, store_mode=12, l2_hints=13, prefetch64=14)
 
 
 class StressResult(C.Structure):

@@ -25,7 +25,8 @@ struct pgsgd_graph {
     std::vector<uint64_t> h_path_off;
 
     NodeRec* d_nodes = nullptr;
-    uint64_t* d_steps = nullptr;
+    int32_t* d_anchor = nullptr;       // [V] x anchors (master copy)
+    StepRec* d_steps = nullptr;
     uint64_t* d_path_off = nullptr;
     uint64_t* d_sample_off = nullptr;  // stress sample offsets [P + 1]
     float* d_zipf_B = nullptr;
@@ -33,6 +34,7 @@ struct pgsgd_graph {
     uint16_t* d_guide = nullptr;       // [n_guide + 1]
     uint32_t n_guide = 1, guide_shift = 0;
     uint32_t* d_flags = nullptr;
+    uint32_t* d_changed = nullptr;     // set by a rebase that moved an anchor
     double* d_partials = nullptr;      // stress scratch [max_stress_blocks][3] + 3 totals
     double* d_per_path = nullptr;      // [P][3]
     double* d_xy = nullptr;            // coordinate staging [V][4]
@@ -48,7 +50,7 @@ struct pgsgd_graph {
     int coord_mode = 0;
     int updates_per_step = 10;
     int block = 256;
-    int blocks_per_sm = 8;
+    int blocks_per_sm = 32;
     int upt = 2;
     int atomic = 0;
     int rebase = 1;
@@ -56,8 +58,9 @@ struct pgsgd_graph {
     int64_t max_concurrent = -1;  // -1 = automatic
     int min_blocks = 1;
     int l2_fetch = 0;
-    int store_mode = 6;  // 64-bit atomic exchange: measured fastest replace-store
-    int load_mode = 0;   // step load operator + 16 * node load operator
+    int store_mode = 1;  // 64-bit atomic exchange: measured fastest replace-store
+    int l2_hints = 1;
+    int pf64 = 3;
 
     // timing
     std::vector<cudaEvent_t> ev_free;
@@ -123,6 +126,8 @@ void free_graph(pgsgd_graph* g) {
     cudaGetDevice(&prev);
     cudaSetDevice(g->device);
     cudaFree(g->d_nodes);
+    cudaFree(g->d_anchor);
+    cudaFree(g->d_changed);
     cudaFree(g->d_steps);
     cudaFree(g->d_path_off);
     cudaFree(g->d_sample_off);
@@ -308,6 +313,8 @@ int pgsgd_create(const uint32_t* node_len, uint32_t n_nodes, const uint64_t* pat
         }                                      \
     }
         TRY(dalloc(g, &g->d_nodes, n_nodes), "node records");
+        TRY(dalloc(g, &g->d_anchor, n_nodes), "node anchors");
+        TRY(dalloc(g, &g->d_changed, 1), "anchor flag");
         TRY(dalloc(g, &g->d_steps, S_), "step records");
         TRY(dalloc(g, &g->d_path_off, n_paths + 1), "path table");
         TRY(dalloc(g, &g->d_sample_off, n_paths + 1), "stress sample table");
@@ -363,13 +370,16 @@ int pgsgd_create(const uint32_t* node_len, uint32_t n_nodes, const uint64_t* pat
                 src_pos = t_pos;
             }
         }
-        TRY(launch_pack_nodes(src_len, n_nodes, g->d_nodes, g->d_flags, g->sm_count, st), "pack nodes");
+        TRY(cudaMemsetAsync(g->d_nodes, 0, (size_t)n_nodes * sizeof(NodeRec), st), "node clear");
+        TRY(cudaMemsetAsync(g->d_anchor, 0, (size_t)n_nodes * sizeof(int32_t), st), "anchor clear");
+        TRY(cudaMemsetAsync(g->d_changed, 0, sizeof(uint32_t), st), "anchor flag clear");
+        TRY(launch_check_lengths(src_len, n_nodes, g->d_flags, g->sm_count, st), "check lengths");
         TRY(launch_pack_steps(src_node, src_rev, src_pos, src_len, n_nodes, g->d_path_off, n_paths, S_,
                               g->d_steps, g->d_flags, g->sm_count, st), "pack steps");
         rc = check_flags(g, st, "pgsgd_create");
         if (rc) break;
         TRY(cudaMalloc(&d_nt, (size_t)n_paths * 8), "extent buffer");
-        TRY(launch_path_extent(g->d_steps, g->d_path_off, g->d_nodes, n_paths, d_nt, st), "path extent");
+        TRY(launch_path_extent(g->d_steps, g->d_path_off, n_paths, d_nt, st), "path extent");
         TRY(cudaMemcpyAsync(nt.data(), d_nt, (size_t)n_paths * 8, cudaMemcpyDeviceToHost, st), "extent readback");
         TRY(cudaStreamSynchronize(st), "create sync");
         for (int64_t v : nt) g->max_path_nt = std::max(g->max_path_nt, v);
@@ -435,14 +445,16 @@ int pgsgd_set_option(pgsgd_graph* g, int option, int64_t v) {
             if (v < 1 || v > 6) return fail(PGSGD_EINVAL, "min blocks must be in [1, 6]");
             g->min_blocks = (int)v;
             return PGSGD_OK;
-        case PGSGD_OPT_LOAD_MODE:
-            if (v < 0 || (v & 15) > 4 || ((v >> 4) != 0 && (v >> 4) != 1 && (v >> 4) != 3))
-                return fail(PGSGD_EINVAL, "load mode: step operator 0..4 plus 16 x node operator 0, 1 or 3");
-            g->load_mode = (int)v;
-            return PGSGD_OK;
         case PGSGD_OPT_STORE_MODE:
-            if (v < 0 || v > 6) return fail(PGSGD_EINVAL, "store mode must be in [0, 6]");
+            if (v != 0 && v != 1) return fail(PGSGD_EINVAL, "store mode must be 0 or 1");
             g->store_mode = (int)v;
+            return PGSGD_OK;
+        case PGSGD_OPT_L2_HINTS:
+            g->l2_hints = v ? 1 : 0;
+            return PGSGD_OK;
+        case PGSGD_OPT_PREFETCH64:
+            if (v < 0 || v > 3) return fail(PGSGD_EINVAL, "prefetch option must be in [0, 3]");
+            g->pf64 = (int)v;
             return PGSGD_OK;
         case PGSGD_OPT_L2_FETCH:
             if (v != 0 && v != 32 && v != 64 && v != 128)
@@ -469,7 +481,8 @@ int pgsgd_get_option(const pgsgd_graph* g, int option, int64_t* v) {
         case PGSGD_OPT_MIN_BLOCKS: *v = g->min_blocks; return PGSGD_OK;
         case PGSGD_OPT_L2_FETCH: *v = g->l2_fetch; return PGSGD_OK;
         case PGSGD_OPT_STORE_MODE: *v = g->store_mode; return PGSGD_OK;
-        case PGSGD_OPT_LOAD_MODE: *v = g->load_mode; return PGSGD_OK;
+        case PGSGD_OPT_L2_HINTS: *v = g->l2_hints; return PGSGD_OK;
+        case PGSGD_OPT_PREFETCH64: *v = g->pf64; return PGSGD_OK;
         default: return fail(PGSGD_EINVAL, "unknown option %d", option);
     }
 }
@@ -497,8 +510,15 @@ int pgsgd_set_coords(pgsgd_graph* g, const double* xy, int on_device, void* cuda
         CK(cudaMemcpyAsync(g->d_xy, xy, bytes, cudaMemcpyHostToDevice, st), "coordinate upload");
         src = g->d_xy;
     }
-    CK(launch_set_coords(src, g->d_nodes, g->n_nodes, g->coord_mode == 0, g->d_flags, g->sm_count, st),
+    CK(launch_set_coords(src, g->d_nodes, g->d_anchor, g->n_nodes, g->coord_mode == 0, g->d_flags, g->sm_count,
+                         st),
        "set coords");
+    // every step record gets its node's new anchor
+    const uint32_t one = 1;
+    CK(cudaMemcpyAsync(g->d_changed, &one, sizeof one, cudaMemcpyHostToDevice, st), "anchor flag");
+    CK(launch_refresh_anchors(g->d_steps, g->d_anchor, g->n_steps, g->d_changed, g->sm_count, st),
+       "refresh anchors");
+    CK(cudaMemsetAsync(g->d_changed, 0, sizeof(uint32_t), st), "anchor flag clear");
     int rc = check_flags(g, st, "pgsgd_set_coords");
     if (rc) return rc;
     g->has_coords = true;
@@ -511,11 +531,11 @@ int pgsgd_get_coords(pgsgd_graph* g, double* xy, int on_device, void* cuda_strea
     cudaStream_t st = S(cuda_stream);
     const size_t bytes = (size_t)g->n_nodes * 4 * sizeof(double);
     if (on_device) {
-        CK(launch_get_coords(g->d_nodes, xy, g->n_nodes, g->sm_count, st), "get coords");
+        CK(launch_get_coords(g->d_nodes, g->d_anchor, xy, g->n_nodes, g->sm_count, st), "get coords");
         return PGSGD_OK;
     }
     if (!g->d_xy) CK(dalloc(g, &g->d_xy, (size_t)g->n_nodes * 4), "coordinate staging");
-    CK(launch_get_coords(g->d_nodes, g->d_xy, g->n_nodes, g->sm_count, st), "get coords");
+    CK(launch_get_coords(g->d_nodes, g->d_anchor, g->d_xy, g->n_nodes, g->sm_count, st), "get coords");
     CK(cudaMemcpyAsync(xy, g->d_xy, bytes, cudaMemcpyDeviceToHost, st), "coordinate download");
     CK(cudaStreamSynchronize(st), "coordinate sync");
     return PGSGD_OK;
@@ -569,8 +589,8 @@ int pgsgd_layout(pgsgd_graph* g, uint32_t iter_max, const double* eta, double et
     L.upt = g->upt;
     L.minb = g->min_blocks;
     L.store_mode = g->store_mode;
-    L.step_load = g->load_mode & 15;
-    L.node_load = g->load_mode >> 4;
+    L.l2_hints = g->l2_hints != 0;
+    L.pf64 = g->pf64;
     L.atomic = g->atomic != 0;
     if (g->l2_fetch) CK(cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, g->l2_fetch), "L2 fetch limit");
     for (uint32_t t = iter_begin; t < iter_end; ++t) {
@@ -589,7 +609,12 @@ int pgsgd_layout(pgsgd_graph* g, uint32_t iter_max, const double* eta, double et
             g->timing_launches += 1;
             g->timing_updates += N;
         }
-        if (g->rebase && g->coord_mode == 0) CK(launch_rebase(g->d_nodes, g->n_nodes, g->sm_count, st), "rebase");
+        if (g->rebase && g->coord_mode == 0) {
+            CK(launch_rebase(g->d_nodes, g->d_anchor, g->n_nodes, g->d_changed, g->sm_count, st), "rebase");
+            CK(launch_refresh_anchors(g->d_steps, g->d_anchor, g->n_steps, g->d_changed, g->sm_count, st),
+               "refresh anchors");
+            CK(cudaMemsetAsync(g->d_changed, 0, sizeof(uint32_t), st), "anchor flag clear");
+        }
     }
     return PGSGD_OK;
 }
@@ -688,8 +713,8 @@ int pgsgd_debug_sample(pgsgd_graph* g, uint32_t t, uint32_t iter_max, double the
     if (rc) return rc;
     rc = ensure_debug(g, count * sizeof(pgsgd_sample));
     if (rc) return rc;
-    CK(launch_debug_sample(sampler_args(g, iter_max, t, (float)theta, seed), u_begin, count, g->d_nodes,
-                           g->d_debug, g->sm_count, st), "debug sample");
+    CK(launch_debug_sample(sampler_args(g, iter_max, t, (float)theta, seed), u_begin, count, g->d_debug,
+                           g->sm_count, st), "debug sample");
     CK(cudaMemcpyAsync(out, g->d_debug, count * sizeof(pgsgd_sample), cudaMemcpyDeviceToHost, st),
        "debug readback");
     CK(cudaStreamSynchronize(st), "debug sync");

@@ -16,103 +16,97 @@
 namespace pgsgd {
 
 constexpr int kZipfTable = 256;     // Zipf acceptance thresholds kept for k < 256
-constexpr int kGuideBuckets = 4096; // path-lookup guide buckets (at most)
+constexpr int kGuideBuckets = 1024; // path-lookup guide buckets (at most)
 
 // ---------------------------------------------------------------- records
 
-// One node of the layout: the two endpoints of its segment (Section II-C:
-// a node is drawn as a line segment) as FP32 offsets from an integer anchor
-// per axis, plus the sequence length the reference distances need. 32 bytes,
-// 32-byte aligned: one DRAM sector holds a whole node (the cache-friendly
-// node record of Section V-B1, sized to a Blackwell sector).
-struct __align__(32) NodeRec {
-    float sx, sy, ex, ey;  // start x, start y, end x, end y (offsets)
-    int32_t ax, ay;        // anchors (0 in plain-FP32 mode)
-    uint32_t len;          // sequence length in nucleotides
-    uint32_t pad;
+// The layout of one node: the two endpoints of its segment (Section II-C: a
+// node is drawn as a line segment). x is an FP32 offset from the node's
+// integer x anchor (0 in plain-FP32 mode); y is plain FP32. 16 bytes: the
+// whole node array of a 5.5 M-node chromosome graph (88 MB) stays resident in
+// the GB300's L2, so the lock-free read-modify-writes of Algorithm 1 hit L2.
+struct __align__(16) NodeRec {
+    float sx, sy, ex, ey;
 };
-static_assert(sizeof(NodeRec) == 32, "node record must fill one sector");
+static_assert(sizeof(NodeRec) == 16, "node record is 16 bytes");
 
-// One path step packed in 64 bits: node id (bits 0-30), orientation (bit 31),
-// nucleotide position where the path enters the step (bits 32-63).
-__host__ __device__ __forceinline__ uint64_t pack_step(uint32_t node, uint32_t rev, uint64_t pos) {
-    return (uint64_t)node | ((uint64_t)(rev & 1u) << 31) | (pos << 32);
-}
-__device__ __forceinline__ uint32_t step_node(uint64_t s) { return (uint32_t)s & 0x7fffffffu; }
-__device__ __forceinline__ uint32_t step_rev(uint64_t s) { return ((uint32_t)s >> 31) & 1u; }
-__device__ __forceinline__ int64_t step_pos(uint64_t s) { return (int64_t)(s >> 32); }
+// One path step (Section V-B1's path data, extended): node id (bits 0-30) and
+// orientation (bit 31), the nucleotide position where the path enters the
+// step, and read-only copies of the node's length and x anchor, so that one
+// 16-byte read gives everything an update needs besides the coordinates.
+struct __align__(16) StepRec {
+    uint32_t nr;   // node | rev << 31
+    uint32_t pos;  // < 2^32
+    uint32_t len;  // node length
+    int32_t ax;    // node's x anchor (refreshed after every rebase)
+};
+static_assert(sizeof(StepRec) == 16, "step record is 16 bytes");
+
+__device__ __forceinline__ uint32_t step_node(const StepRec& s) { return s.nr & 0x7fffffffu; }
+__device__ __forceinline__ uint32_t step_rev(const StepRec& s) { return s.nr >> 31; }
 
 // Path position of endpoint e (0 = start point, 1 = end point) of a step: a
 // step taken in reverse meets its node's end point first.
-__device__ __forceinline__ int64_t endpoint_pos(uint64_t s, uint32_t e, uint32_t len) {
-    return step_pos(s) + (((e ^ step_rev(s)) & 1u) ? (int64_t)len : 0);
+__device__ __forceinline__ int64_t endpoint_pos(const StepRec& s, uint32_t e) {
+    return (int64_t)s.pos + (((e ^ step_rev(s)) & 1u) ? (int64_t)s.len : 0);
 }
 
 // ---------------------------------------------------------------- memory access
 
-// Packed step records: one random 8-byte read per record. Read at L2 (.cg)
-// so the request is a single 32-byte sector; through the L1/texture path an
-// isolated miss pulled the whole 128-byte line from L2 and DRAM.
-__device__ __forceinline__ uint64_t load_step(const uint64_t* p) {
-    uint64_t v;
-    asm volatile("ld.global.cg.u64 %0, [%1];" : "=l"(v) : "l"(p));
-    return v;
+// L2 residency policies: step records are streamed (evict first), node
+// records are the hot working set (evict last).
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
 }
 
-// Step-record load with a selectable cache operator (mode 0 = .cg).
-__device__ __forceinline__ uint64_t load_step_mode(const uint64_t* p, int mode) {
-    uint64_t v;
-    switch (mode) {
-        case 1: asm volatile("ld.global.cg.L2::64B.u64 %0, [%1];" : "=l"(v) : "l"(p)); break;
-        case 2: asm volatile("ld.global.nc.L1::no_allocate.u64 %0, [%1];" : "=l"(v) : "l"(p)); break;
-        case 3: asm volatile("ld.global.cv.u64 %0, [%1];" : "=l"(v) : "l"(p)); break;
-        case 4: asm volatile("ld.global.lu.u64 %0, [%1];" : "=l"(v) : "l"(p)); break;
-        default: asm volatile("ld.global.cg.u64 %0, [%1];" : "=l"(v) : "l"(p)); break;
-    }
-    return v;
-}
-
-// Node records change during a launch (Hogwild!): read them from L2 (.cg),
-// never from a possibly stale L1 line, with one 256-bit load per node.
-__device__ __forceinline__ NodeRec unpack_node(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                               uint32_t a4, uint32_t a5, uint32_t a6, uint32_t a7) {
-    NodeRec r;
-    r.sx = __uint_as_float(a0); r.sy = __uint_as_float(a1);
-    r.ex = __uint_as_float(a2); r.ey = __uint_as_float(a3);
-    r.ax = (int32_t)a4; r.ay = (int32_t)a5; r.len = a6; r.pad = a7;
+// One random step record: a single 16-byte read at L2 (.cg), one sector.
+// pf64 adds the 64-byte L2 prefetch-size hint.
+__device__ __forceinline__ StepRec load_step(const StepRec* p, uint64_t pol, bool pf64 = false) {
+    StepRec r;
+    uint32_t ax;
+    if (pf64)
+        asm volatile("ld.global.cg.L2::cache_hint.L2::64B.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+                     : "=r"(r.nr), "=r"(r.pos), "=r"(r.len), "=r"(ax)
+                     : "l"(p), "l"(pol));
+    else
+        asm volatile("ld.global.cg.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+                     : "=r"(r.nr), "=r"(r.pos), "=r"(r.len), "=r"(ax)
+                     : "l"(p), "l"(pol));
+    r.ax = (int32_t)ax;
     return r;
 }
 
-__device__ __forceinline__ NodeRec load_node(const NodeRec* p) {
-    uint32_t a0, a1, a2, a3, a4, a5, a6, a7;
-    asm volatile("ld.global.cg.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(a0), "=r"(a1), "=r"(a2), "=r"(a3), "=r"(a4), "=r"(a5), "=r"(a6), "=r"(a7)
-                 : "l"(p));
-    return unpack_node(a0, a1, a2, a3, a4, a5, a6, a7);
+// Node records change during a launch (Hogwild!): read them at L2 (.cg),
+// never from a possibly stale L1 line.
+__device__ __forceinline__ NodeRec load_node(const NodeRec* p, uint64_t pol, bool pf64 = false) {
+    NodeRec r;
+    if (pf64)
+        asm volatile("ld.global.cg.L2::cache_hint.L2::64B.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+                     : "=f"(r.sx), "=f"(r.sy), "=f"(r.ex), "=f"(r.ey)
+                     : "l"(p), "l"(pol));
+    else
+        asm volatile("ld.global.cg.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+                     : "=f"(r.sx), "=f"(r.sy), "=f"(r.ex), "=f"(r.ey)
+                     : "l"(p), "l"(pol));
+    return r;
 }
 
-// Node-record load with a selectable cache operator (mode 0 = .cg; modes that
-// could return stale data within a launch are not offered).
-__device__ __forceinline__ NodeRec load_node_mode(const NodeRec* p, int mode) {
-    uint32_t a0, a1, a2, a3, a4, a5, a6, a7;
-    switch (mode) {
-        case 1:
-            asm volatile("ld.global.cg.L2::64B.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                         : "=r"(a0), "=r"(a1), "=r"(a2), "=r"(a3), "=r"(a4), "=r"(a5), "=r"(a6), "=r"(a7)
-                         : "l"(p));
-            break;
-        case 3:
-            asm volatile("ld.global.cv.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                         : "=r"(a0), "=r"(a1), "=r"(a2), "=r"(a3), "=r"(a4), "=r"(a5), "=r"(a6), "=r"(a7)
-                         : "l"(p));
-            break;
-        default:
-            asm volatile("ld.global.cg.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                         : "=r"(a0), "=r"(a1), "=r"(a2), "=r"(a3), "=r"(a4), "=r"(a5), "=r"(a6), "=r"(a7)
-                         : "l"(p));
-            break;
-    }
-    return unpack_node(a0, a1, a2, a3, a4, a5, a6, a7);
+// Write one moved point (8 bytes) by replacing it: a 64-bit atomic exchange
+// executed at L2 (last writer wins, like the paper's racy stores, but on
+// GB300 several times faster than any st.global form for this pattern).
+__device__ __forceinline__ void exchange_point(float* p, float x, float y, uint64_t pol) {
+    const unsigned long long v = ((unsigned long long)__float_as_uint(y) << 32) | __float_as_uint(x);
+    unsigned long long old;
+    asm volatile("atom.global.exch.L2::cache_hint.b64 %0, [%1], %2, %3;"
+                 : "=l"(old) : "l"(p), "l"(v), "l"(pol) : "memory");
+    (void)old;
 }
 
 // ---------------------------------------------------------------- Philox4x32-10
@@ -279,7 +273,7 @@ __device__ __forceinline__ bool zipf_trial(const ZipfConsts& z, const float* T, 
 // ---------------------------------------------------------------- the pair draw
 
 struct SamplerArgs {
-    const uint64_t* steps;     // packed step records [S]
+    const StepRec* steps;      // step records [S]
     const uint64_t* path_off;  // [P + 1]
     const float* zipf_B;       // [P] H(n_p - 1/2); unused for n_p < 2
     const float* zipf_T;       // [kZipfTable] H(k + 1/2) - h(k) for the current theta

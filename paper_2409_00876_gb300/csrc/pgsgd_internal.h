@@ -29,13 +29,14 @@ struct UpdateLaunch {
     uint64_t n_updates;  // updates in this launch
     float eta;
     int block, grid, upt, minb;
-    int store_mode;
-    int step_load, node_load;  // cache operators of the record loads
+    int store_mode;      // 0 = plain store, 1 = 64-bit atomic exchange
+    bool l2_hints;       // evict-first step records, evict-last node records
+    int pf64;            // 64-byte L2 prefetch hint: bit 0 step loads, bit 1 node loads
     bool atomic;
 };
 
 struct StressLaunch {
-    const uint64_t* steps;
+    const StepRec* steps;
     const uint64_t* path_off;   // [P + 1]
     const uint64_t* sample_off; // [P + 1] first sample index of every path
     const NodeRec* nodes;
@@ -47,32 +48,36 @@ struct StressLaunch {
     int block, grid;
 };
 
-size_t update_smem_bytes(uint32_t n_paths, uint32_t n_guide);
+// Shared memory of the staged path tables (offsets, Zipf thresholds, Zipf B, guide).
+__host__ __device__ inline size_t update_smem_bytes(uint32_t n_paths, uint32_t n_guide) {
+    return (size_t)(n_paths + 1) * sizeof(uint64_t) + (size_t)(kZipfTable + n_paths) * sizeof(float) +
+           (size_t)(n_guide + 1) * sizeof(uint16_t);
+}
 size_t stress_smem_bytes(uint32_t n_paths);
 
-cudaError_t launch_pack_nodes(const uint32_t* node_len, uint32_t n, NodeRec* nodes,
-                              uint32_t* flags, int sm_count, cudaStream_t st);
-cudaError_t launch_pack_steps(const uint32_t* step_node, const uint8_t* step_rev,
-                              const int64_t* step_pos, const uint32_t* node_len,
-                              uint32_t n_nodes, const uint64_t* path_off, uint32_t n_paths,
-                              uint64_t n_steps, uint64_t* steps, uint32_t* flags,
+cudaError_t launch_check_lengths(const uint32_t* node_len, uint32_t n, uint32_t* flags, int sm_count,
+                                 cudaStream_t st);
+cudaError_t launch_pack_steps(const uint32_t* step_node, const uint8_t* step_rev, const int64_t* step_pos,
+                              const uint32_t* node_len, uint32_t n_nodes, const uint64_t* path_off,
+                              uint32_t n_paths, uint64_t n_steps, StepRec* steps, uint32_t* flags,
                               int sm_count, cudaStream_t st);
-cudaError_t launch_path_extent(const uint64_t* steps, const uint64_t* path_off,
-                               const NodeRec* nodes, uint32_t n_paths, int64_t* out_nt,
-                               cudaStream_t st);
-cudaError_t launch_set_coords(const double* xy, NodeRec* nodes, uint32_t n, int anchored,
+cudaError_t launch_path_extent(const StepRec* steps, const uint64_t* path_off, uint32_t n_paths,
+                               int64_t* out_nt, cudaStream_t st);
+cudaError_t launch_set_coords(const double* xy, NodeRec* nodes, int32_t* anchor, uint32_t n, int anchored,
                               uint32_t* flags, int sm_count, cudaStream_t st);
-cudaError_t launch_get_coords(const NodeRec* nodes, double* xy, uint32_t n, int sm_count,
-                              cudaStream_t st);
-cudaError_t launch_rebase(NodeRec* nodes, uint32_t n, int sm_count, cudaStream_t st);
-cudaError_t launch_zipf_setup(const uint64_t* path_off, uint32_t n_paths, float theta,
-                              float* zipf_B, float* zipf_T, cudaStream_t st);
+cudaError_t launch_get_coords(const NodeRec* nodes, const int32_t* anchor, double* xy, uint32_t n,
+                              int sm_count, cudaStream_t st);
+cudaError_t launch_rebase(NodeRec* nodes, int32_t* anchor, uint32_t n, uint32_t* changed, int sm_count,
+                          cudaStream_t st);
+cudaError_t launch_refresh_anchors(StepRec* steps, const int32_t* anchor, uint64_t n_steps,
+                                   const uint32_t* changed, int sm_count, cudaStream_t st);
+cudaError_t launch_zipf_setup(const uint64_t* path_off, uint32_t n_paths, float theta, float* zipf_B,
+                              float* zipf_T, cudaStream_t st);
 cudaError_t launch_update(const UpdateLaunch& L, cudaStream_t st);
-cudaError_t launch_debug_sample(const SamplerArgs& s, uint64_t u_begin, uint64_t count,
-                                const NodeRec* nodes, void* out, int sm_count, cudaStream_t st);
-cudaError_t launch_debug_sweep(const SamplerArgs& s, uint64_t u_begin, uint64_t count,
-                               const NodeRec* nodes, float eta, float4* out, int sm_count,
-                               cudaStream_t st);
+cudaError_t launch_debug_sample(const SamplerArgs& s, uint64_t u_begin, uint64_t count, void* out,
+                                int sm_count, cudaStream_t st);
+cudaError_t launch_debug_sweep(const SamplerArgs& s, uint64_t u_begin, uint64_t count, const NodeRec* nodes,
+                               float eta, float4* out, int sm_count, cudaStream_t st);
 cudaError_t launch_stress(const StressLaunch& L, cudaStream_t st);
 cudaError_t launch_stress_finalize(const double* partials, int n, double* out3, cudaStream_t st);
 

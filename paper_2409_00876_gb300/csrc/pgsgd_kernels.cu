@@ -1,14 +1,14 @@
 // CUDA kernels of the PG-SGD path for GB300 (sm_103a): graph ingest and
 // validation, the lock-free update kernel of Algorithm 1, the sampled
-// path-stress kernel of Eq. 2, coordinate conversion and the debug kernels
-// that expose the sampler and a Jacobi sweep for parity checks.
+// path-stress kernel of Eq. 2, coordinate conversion and anchor upkeep, and
+// the debug kernels that expose the sampler and a Jacobi sweep for parity
+// checks.
 //
-// The path is a random gather/scatter over HBM (Section III-B: memory bound,
-// no dense contraction), so there are no tensor cores here: the design goal is
-// bytes per update. Each update reads two 8-byte step records and two 32-byte
-// node records (one DRAM sector each) and writes back 8 bytes of each node.
-#include <cstdio>
-
+// The path is random gathers and scatters over HBM (Section III-B: memory
+// bound, no dense contraction), so there are no tensor cores here. An update
+// reads two 16-byte step records (streamed, evict-first in L2) and two
+// 16-byte node records (the L2-resident working set, evict-last), and writes
+// back 8 bytes of each node with an atomic exchange at L2.
 #include "../../include/pgsgd.h"
 #include "pgsgd_internal.h"
 
@@ -16,26 +16,13 @@ namespace pgsgd {
 
 namespace {
 
-__device__ __forceinline__ uint32_t find_off(const uint64_t* off, uint32_t P, uint64_t g) {
-    return find_path(off, P, g);
-}
-
 // ---------------------------------------------------------------- ingest
 
-__global__ void pack_nodes_kernel(const uint32_t* __restrict__ node_len, uint32_t n,
-                                  NodeRec* __restrict__ nodes, uint32_t* flags) {
+__global__ void check_lengths_kernel(const uint32_t* __restrict__ node_len, uint32_t n, uint32_t* flags) {
     uint32_t bad = 0;
     for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
-         v += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t len = node_len[v];
-        if (len == 0) bad |= FLAG_ZERO_LEN;
-        NodeRec r;
-        r.sx = r.sy = r.ex = r.ey = 0.0f;
-        r.ax = r.ay = 0;
-        r.len = len;
-        r.pad = 0;
-        nodes[v] = r;
-    }
+         v += (uint64_t)gridDim.x * blockDim.x)
+        if (node_len[v] == 0) bad |= FLAG_ZERO_LEN;
     if (bad) atomicOr(flags, bad);
 }
 
@@ -44,115 +31,126 @@ __global__ void pack_steps_kernel(const uint32_t* __restrict__ step_node,
                                   const int64_t* __restrict__ step_pos,
                                   const uint32_t* __restrict__ node_len, uint32_t n_nodes,
                                   const uint64_t* __restrict__ path_off, uint32_t P, uint64_t S,
-                                  uint64_t* __restrict__ steps, uint32_t* flags) {
+                                  StepRec* __restrict__ steps, uint32_t* flags) {
     extern __shared__ uint64_t s_off[];
     for (uint32_t k = threadIdx.x; k <= P; k += blockDim.x) s_off[k] = path_off[k];
     __syncthreads();
     uint32_t bad = 0;
     for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < S;
          s += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t p = find_off(s_off, P, s);
+        const uint32_t p = find_path(s_off, P, s);
         const bool first = s == s_off[p];
         const bool last = s + 1 == s_off[p + 1];
         const uint32_t nd = step_node[s];
         const uint32_t rv = step_rev[s];
         const int64_t ps = step_pos[s];
-        if (nd >= n_nodes) bad |= FLAG_BAD_NODE;
+        const bool nd_ok = nd < n_nodes;
+        if (!nd_ok) bad |= FLAG_BAD_NODE;
         if (rv > 1) bad |= FLAG_BAD_REV;
         if (ps < 0 || ps >= (int64_t)(1ll << 32)) bad |= FLAG_POS_RANGE;
         if (first && ps != 0) bad |= FLAG_BAD_POS;
-        if (!last && nd < n_nodes && step_pos[s + 1] != ps + (int64_t)node_len[nd])
-            bad |= FLAG_BAD_POS;
-        steps[s] = pack_step(nd & 0x7fffffffu, rv, (uint64_t)ps & 0xffffffffull);
+        const uint32_t len = nd_ok ? node_len[nd] : 0u;
+        if (!last && nd_ok && step_pos[s + 1] != ps + (int64_t)len) bad |= FLAG_BAD_POS;
+        StepRec r;
+        r.nr = (nd & 0x7fffffffu) | ((rv & 1u) << 31);
+        r.pos = (uint32_t)ps;
+        r.len = len;
+        r.ax = 0;
+        steps[s] = r;
     }
     if (bad) atomicOr(flags, bad);
 }
 
-__global__ void path_extent_kernel(const uint64_t* __restrict__ steps,
-                                   const uint64_t* __restrict__ path_off,
-                                   const NodeRec* __restrict__ nodes, uint32_t P,
-                                   int64_t* __restrict__ out_nt) {
+__global__ void path_extent_kernel(const StepRec* __restrict__ steps, const uint64_t* __restrict__ path_off,
+                                   uint32_t P, int64_t* __restrict__ out_nt) {
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P) return;
     const uint64_t a = path_off[p], b = path_off[p + 1];
     if (a == b) { out_nt[p] = 0; return; }
-    const uint64_t s = steps[b - 1];
-    out_nt[p] = step_pos(s) + (int64_t)nodes[step_node(s)].len;
+    const StepRec s = steps[b - 1];
+    out_nt[p] = (int64_t)s.pos + (int64_t)s.len;
 }
 
-// ---------------------------------------------------------------- coordinates
+// ---------------------------------------------------------------- coordinates and anchors
 
 __global__ void set_coords_kernel(const double* __restrict__ xy, NodeRec* __restrict__ nodes,
-                                  uint32_t n, int anchored, uint32_t* flags) {
+                                  int32_t* __restrict__ anchor, uint32_t n, int anchored,
+                                  uint32_t* flags) {
     uint32_t bad = 0;
     for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
          v += (uint64_t)gridDim.x * blockDim.x) {
         const double sx = xy[4 * v], sy = xy[4 * v + 1], ex = xy[4 * v + 2], ey = xy[4 * v + 3];
         if (!isfinite(sx) || !isfinite(sy) || !isfinite(ex) || !isfinite(ey)) bad |= FLAG_COORD_NAN;
-        NodeRec r = nodes[v];
-        int32_t ax = 0, ay = 0;
+        int32_t ax = 0;
         if (anchored) {
-            // Anchor an axis only where FP32 would lose sub-nucleotide
-            // resolution; below 4096 the FP32 value itself is kept exactly.
+            // anchor x only where FP32 would lose sub-nucleotide resolution;
+            // below 4096 the FP32 value itself is kept exactly
             const double lim = 1073741824.0;  // 2^30
-            if (fabs(sx) >= lim || fabs(sy) >= lim || fabs(ex) >= lim || fabs(ey) >= lim)
-                bad |= FLAG_COORD_RANGE;
-            else {
-                ax = fabs(sx) >= 4096.0 ? (int32_t)rint(sx) : 0;
-                ay = fabs(sy) >= 4096.0 ? (int32_t)rint(sy) : 0;
-            }
+            if (fabs(sx) >= lim || fabs(ex) >= lim) bad |= FLAG_COORD_RANGE;
+            else ax = fabs(sx) >= 4096.0 ? (int32_t)rint(sx) : 0;
         }
-        r.ax = ax;
-        r.ay = ay;
+        anchor[v] = ax;
+        NodeRec r;
         r.sx = (float)(sx - ax);
-        r.sy = (float)(sy - ay);
+        r.sy = (float)sy;
         r.ex = (float)(ex - ax);
-        r.ey = (float)(ey - ay);
+        r.ey = (float)ey;
         nodes[v] = r;
     }
     if (bad) atomicOr(flags, bad);
 }
 
-__global__ void get_coords_kernel(const NodeRec* __restrict__ nodes, double* __restrict__ xy,
-                                  uint32_t n) {
+__global__ void get_coords_kernel(const NodeRec* __restrict__ nodes, const int32_t* __restrict__ anchor,
+                                  double* __restrict__ xy, uint32_t n) {
     for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
          v += (uint64_t)gridDim.x * blockDim.x) {
         const NodeRec r = nodes[v];
-        xy[4 * v] = (double)r.ax + (double)r.sx;
-        xy[4 * v + 1] = (double)r.ay + (double)r.sy;
-        xy[4 * v + 2] = (double)r.ax + (double)r.ex;
-        xy[4 * v + 3] = (double)r.ay + (double)r.ey;
+        const double ax = (double)anchor[v];
+        xy[4 * v] = ax + (double)r.sx;
+        xy[4 * v + 1] = (double)r.sy;
+        xy[4 * v + 2] = ax + (double)r.ex;
+        xy[4 * v + 3] = (double)r.ey;
     }
 }
 
-// Move an anchor to the rounded start point once its offset has drifted past
-// 8, so offsets stay small: an FP32 offset below 8 resolves 1e-6 nt, while one
-// near 4096 would only resolve 2.4e-4 nt. Subtracting an integer within half
-// a unit of sx leaves sx exact.
-__global__ void rebase_kernel(NodeRec* __restrict__ nodes, uint32_t n) {
+// Move a node's x anchor to its rounded start point once the start offset
+// has drifted past 8, so offsets stay small: an FP32 offset below 8 resolves
+// 1e-6 nt. Subtracting an integer within half a unit of sx leaves sx exact.
+// Sets *changed when any anchor moved.
+__global__ void rebase_kernel(NodeRec* __restrict__ nodes, int32_t* __restrict__ anchor, uint32_t n,
+                              uint32_t* changed) {
+    int any = 0;
     for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
          v += (uint64_t)gridDim.x * blockDim.x) {
         NodeRec r = nodes[v];
-        bool changed = false;
         if (fabsf(r.sx) > 8.0f) {
             const float sh = rintf(r.sx);
-            const int64_t na = (int64_t)r.ax + (int64_t)sh;
+            const int64_t na = (int64_t)anchor[v] + (int64_t)sh;
             if (na > -(1ll << 30) && na < (1ll << 30)) {
-                r.ax = (int32_t)na; r.sx -= sh; r.ex -= sh; changed = true;
+                anchor[v] = (int32_t)na;
+                r.sx -= sh;
+                r.ex -= sh;
+                nodes[v] = r;
+                any = 1;
             }
         }
-        if (fabsf(r.sy) > 8.0f) {
-            const float sh = rintf(r.sy);
-            const int64_t na = (int64_t)r.ay + (int64_t)sh;
-            if (na > -(1ll << 30) && na < (1ll << 30)) {
-                r.ay = (int32_t)na; r.sy -= sh; r.ey -= sh; changed = true;
-            }
-        }
-        if (changed) nodes[v] = r;
+    }
+    if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(changed, 1u);
+}
+
+// Copy every node's current anchor into the step records that visit it; does
+// nothing unless *changed is set.
+__global__ void refresh_anchors_kernel(StepRec* __restrict__ steps, const int32_t* __restrict__ anchor,
+                                       uint64_t S, const uint32_t* __restrict__ changed) {
+    if (*changed == 0) return;
+    for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < S;
+         s += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t nd = steps[s].nr & 0x7fffffffu;
+        steps[s].ax = anchor[nd];
     }
 }
 
-// ---------------------------------------------------------------- Zipf per path
+// ---------------------------------------------------------------- Zipf per theta
 
 // Per-theta tables: B[p] = H(n_p - 1/2) for every path, and the acceptance
 // thresholds T[k] = H(k + 1/2) - h(k) for k < 256 (T[0] unused).
@@ -197,15 +195,15 @@ struct Move {
 
 // The update of Zheng et al. that Algorithm 1, line 15 applies (Fig. 3):
 // w = d^-2, mu = min(eta w, 1), r = mu (|v_i - v_j| - d) / (2 |v_i - v_j|),
-// v_i -= r (v_i - v_j), v_j += r (v_i - v_j). FP32, anchors differenced in
+// v_i -= r (v_i - v_j), v_j += r (v_i - v_j). FP32; x anchors differenced in
 // integers so chromosome-scale coordinates keep their resolution.
-__device__ __forceinline__ Move pair_move(const NodeRec& a, uint32_t ea, const NodeRec& b,
-                                          uint32_t eb, int64_t d, float eta) {
+__device__ __forceinline__ Move pair_move(const NodeRec& a, int32_t axa, uint32_t ea, const NodeRec& b,
+                                          int32_t axb, uint32_t eb, int64_t d, float eta) {
     Move m;
     const float xa = ea ? a.ex : a.sx, ya = ea ? a.ey : a.sy;
     const float xb = eb ? b.ex : b.sx, yb = eb ? b.ey : b.sy;
-    const float dx = __ll2float_rn((int64_t)a.ax - (int64_t)b.ax) + (xa - xb);
-    const float dy = __ll2float_rn((int64_t)a.ay - (int64_t)b.ay) + (ya - yb);
+    const float dx = __ll2float_rn((int64_t)axa - (int64_t)axb) + (xa - xb);
+    const float dy = ya - yb;
     const float mag = sqrtf(dx * dx + dy * dy);
     m.moved = mag > 0.0f;
     const float df = __ll2float_rn(d);
@@ -217,90 +215,81 @@ __device__ __forceinline__ Move pair_move(const NodeRec& a, uint32_t ea, const N
     return m;
 }
 
-// Write one moved point (8 bytes). The cache operator is selectable.
-__device__ __forceinline__ void store_point(float* p, float x, float y, int mode) {
-    switch (mode) {
-        case 1: asm volatile("st.global.cg.v2.f32 [%0], {%1, %2};" :: "l"(p), "f"(x), "f"(y) : "memory"); break;
-        case 2: asm volatile("st.global.cs.v2.f32 [%0], {%1, %2};" :: "l"(p), "f"(x), "f"(y) : "memory"); break;
-        case 3: asm volatile("st.global.wt.v2.f32 [%0], {%1, %2};" :: "l"(p), "f"(x), "f"(y) : "memory"); break;
-        case 4: asm volatile("st.relaxed.gpu.global.v2.f32 [%0], {%1, %2};" :: "l"(p), "f"(x), "f"(y) : "memory"); break;
-        case 5: asm volatile("st.global.L1::no_allocate.v2.f32 [%0], {%1, %2};" :: "l"(p), "f"(x), "f"(y) : "memory"); break;
-        case 6: {  // exchange: an atomic that replaces instead of adding
-            unsigned long long v = ((unsigned long long)__float_as_uint(y) << 32) | __float_as_uint(x);
-            atomicExch(reinterpret_cast<unsigned long long*>(p), v);
-            break;
-        }
-        default: *reinterpret_cast<float2*>(p) = make_float2(x, y); break;
-    }
-}
-
 // ---------------------------------------------------------------- the update kernel
 
 // One launch = one iteration's N updates (or a slice), grid-stride over the
 // update index u. Every thread keeps UPT independent updates in flight per
 // loop trip: all draws first (ALU), then all step-record loads, then all
-// node-record loads, then the moves, so that 2 * UPT DRAM requests per
-// thread overlap instead of queueing behind each other.
+// node-record loads, then the moves.
 template <int UPT, int MINB>
 __global__ void __launch_bounds__(256, MINB) update_kernel(UpdateLaunch L) {
-    const bool ATOMIC = L.atomic;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ ZipfConsts zc;
     const PathTable pt = stage_paths(L.s, smem, zc);
     SamplerArgs a = L.s;
     a.zc = zc;
+    const uint64_t pol_stream = L.l2_hints ? policy_evict_first() : 0;
+    const uint64_t pol_keep = L.l2_hints ? policy_evict_last() : 0;
     const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t gtid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    const uint64_t* __restrict__ steps = a.steps;
+    const StepRec* __restrict__ steps = a.steps;
     NodeRec* __restrict__ nodes = L.nodes;
     for (uint64_t base = gtid; base < L.n_updates; base += nthr * UPT) {
-        Pair pr[UPT];
+        uint64_t gi[UPT], gj[UPT];
+        uint32_t w2[UPT];
         bool act[UPT];
 #pragma unroll
         for (int k = 0; k < UPT; ++k) {
             const uint64_t u = base + (uint64_t)k * nthr;
             act[k] = u < L.n_updates;
             if (act[k]) {
-                pr[k] = draw_pair(a, pt, L.u_begin + u);
-                act[k] = !pr[k].short_path;
+                const Pair pr = draw_pair(a, pt, L.u_begin + u);
+                act[k] = !pr.short_path;
+                gi[k] = pr.base + pr.i;
+                gj[k] = pr.base + pr.j;
+                w2[k] = pr.w2;
             }
         }
-        uint64_t si[UPT], sj[UPT];
+        StepRec si[UPT], sj[UPT];
 #pragma unroll
         for (int k = 0; k < UPT; ++k) {
             if (act[k]) {
-                si[k] = load_step_mode(steps + pr[k].base + pr[k].i, L.step_load);
-                sj[k] = load_step_mode(steps + pr[k].base + pr[k].j, L.step_load);
+                si[k] = load_step(steps + gi[k], pol_stream, L.pf64 & 1);
+                sj[k] = load_step(steps + gj[k], pol_stream, L.pf64 & 1);
             }
         }
         NodeRec na[UPT], nb[UPT];
 #pragma unroll
         for (int k = 0; k < UPT; ++k) {
             if (act[k]) {
-                na[k] = load_node_mode(nodes + step_node(si[k]), L.node_load);
-                nb[k] = load_node_mode(nodes + step_node(sj[k]), L.node_load);
+                na[k] = load_node(nodes + step_node(si[k]), pol_keep, L.pf64 & 2);
+                nb[k] = load_node(nodes + step_node(sj[k]), pol_keep, L.pf64 & 2);
             }
         }
 #pragma unroll
         for (int k = 0; k < UPT; ++k) {
             if (!act[k]) continue;
-            const uint32_t ea = (pr[k].w2 >> 2) & 1u, eb = (pr[k].w2 >> 3) & 1u;
-            const int64_t pa = endpoint_pos(si[k], ea, na[k].len);
-            const int64_t pb = endpoint_pos(sj[k], eb, nb[k].len);
+            const uint32_t ea = (w2[k] >> 2) & 1u, eb = (w2[k] >> 3) & 1u;
+            const int64_t pa = endpoint_pos(si[k], ea), pb = endpoint_pos(sj[k], eb);
             const int64_t d = pa > pb ? pa - pb : pb - pa;
             if (d == 0) continue;
-            const Move m = pair_move(na[k], ea, nb[k], eb, d, L.eta);
+            const Move m = pair_move(na[k], si[k].ax, ea, nb[k], sj[k].ax, eb, d, L.eta);
             if (!m.moved) continue;
             float* pa_ptr = &nodes[step_node(si[k])].sx + 2 * ea;
             float* pb_ptr = &nodes[step_node(sj[k])].sx + 2 * eb;
-            if (ATOMIC) {
+            if (L.atomic) {
                 atomicAdd(reinterpret_cast<float2*>(pa_ptr), make_float2(m.dxi, m.dyi));
                 atomicAdd(reinterpret_cast<float2*>(pb_ptr), make_float2(m.dxj, m.dyj));
             } else {
                 const float xa = ea ? na[k].ex : na[k].sx, ya = ea ? na[k].ey : na[k].sy;
                 const float xb = eb ? nb[k].ex : nb[k].sx, yb = eb ? nb[k].ey : nb[k].sy;
-                store_point(pa_ptr, xa + m.dxi, ya + m.dyi, L.store_mode);
-                store_point(pb_ptr, xb + m.dxj, yb + m.dyj, L.store_mode);
+                if (L.store_mode == 0) {
+                    *reinterpret_cast<float2*>(pa_ptr) = make_float2(xa + m.dxi, ya + m.dyi);
+                    *reinterpret_cast<float2*>(pb_ptr) = make_float2(xb + m.dxj, yb + m.dyj);
+                } else {
+                    exchange_point(pa_ptr, xa + m.dxi, ya + m.dyi, pol_keep);
+                    exchange_point(pb_ptr, xb + m.dxj, yb + m.dyj, pol_keep);
+                }
             }
         }
     }
@@ -308,8 +297,7 @@ __global__ void __launch_bounds__(256, MINB) update_kernel(UpdateLaunch L) {
 
 // ---------------------------------------------------------------- debug kernels
 
-__global__ void debug_sample_kernel(SamplerArgs a0, uint64_t u_begin, uint64_t count,
-                                    const NodeRec* __restrict__ nodes, pgsgd_sample* out) {
+__global__ void debug_sample_kernel(SamplerArgs a0, uint64_t u_begin, uint64_t count, pgsgd_sample* out) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ ZipfConsts zc;
     const PathTable pt = stage_paths(a0, smem, zc);
@@ -327,10 +315,8 @@ __global__ void debug_sample_kernel(SamplerArgs a0, uint64_t u_begin, uint64_t c
         if (pr.short_path) {
             r.skip = 1;
         } else {
-            const uint64_t si = load_step(a.steps + pr.base + pr.i);
-            const uint64_t sj = load_step(a.steps + pr.base + pr.j);
-            const int64_t pa = endpoint_pos(si, r.e_i, nodes[step_node(si)].len);
-            const int64_t pb = endpoint_pos(sj, r.e_j, nodes[step_node(sj)].len);
+            const StepRec si = a.steps[pr.base + pr.i], sj = a.steps[pr.base + pr.j];
+            const int64_t pa = endpoint_pos(si, r.e_i), pb = endpoint_pos(sj, r.e_j);
             r.d_ref = pa > pb ? pa - pb : pb - pa;
             r.skip = r.d_ref == 0 ? 2 : 0;
         }
@@ -350,15 +336,13 @@ __global__ void debug_sweep_kernel(SamplerArgs a0, uint64_t u_begin, uint64_t co
         const Pair pr = draw_pair(a, pt, u_begin + q);
         float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
         if (!pr.short_path) {
-            const uint64_t si = load_step(a.steps + pr.base + pr.i);
-            const uint64_t sj = load_step(a.steps + pr.base + pr.j);
-            const NodeRec na = load_node(nodes + step_node(si));
-            const NodeRec nb = load_node(nodes + step_node(sj));
+            const StepRec si = a.steps[pr.base + pr.i], sj = a.steps[pr.base + pr.j];
+            const NodeRec na = nodes[step_node(si)], nb = nodes[step_node(sj)];
             const uint32_t ea = (pr.w2 >> 2) & 1u, eb = (pr.w2 >> 3) & 1u;
-            const int64_t pa = endpoint_pos(si, ea, na.len), pb = endpoint_pos(sj, eb, nb.len);
+            const int64_t pa = endpoint_pos(si, ea), pb = endpoint_pos(sj, eb);
             const int64_t d = pa > pb ? pa - pb : pb - pa;
             if (d != 0) {
-                const Move m = pair_move(na, ea, nb, eb, d, eta);
+                const Move m = pair_move(na, si.ax, ea, nb, sj.ax, eb, d, eta);
                 if (m.moved) o = make_float4(m.dxi, m.dyi, m.dxj, m.dyj);
             }
         }
@@ -378,6 +362,8 @@ __global__ void stress_kernel(StressLaunch L) {
         s_poff[k] = L.path_off[k];
     }
     __syncthreads();
+    const uint64_t pol_stream = policy_evict_first();
+    const uint64_t pol_keep = policy_evict_last();
     const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t gtid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     double sum = 0.0, sq = 0.0, cnt = 0.0;
@@ -386,7 +372,7 @@ __global__ void stress_kernel(StressLaunch L) {
     double ps = 0.0, pq = 0.0, pc = 0.0;
     for (uint64_t base = gtid; base < L.n_samples; base += nthr * SPT) {
         uint32_t p[SPT];
-        uint64_t si[SPT], sj[SPT];
+        StepRec si[SPT], sj[SPT];
         uint32_t ei[SPT], ej[SPT];
         bool act[SPT];
 #pragma unroll
@@ -406,27 +392,26 @@ __global__ void stress_kernel(StressLaunch L) {
             const uint64_t j = x + (x >= i);
             ei[k] = w.z & 1u;
             ej[k] = (w.z >> 1) & 1u;
-            si[k] = load_step(L.steps + off + i);
-            sj[k] = load_step(L.steps + off + j);
+            si[k] = load_step(L.steps + off + i, pol_stream);
+            sj[k] = load_step(L.steps + off + j, pol_stream);
         }
         NodeRec na[SPT], nb[SPT];
 #pragma unroll
         for (int k = 0; k < SPT; ++k) {
             if (!act[k]) continue;
-            na[k] = load_node(L.nodes + step_node(si[k]));
-            nb[k] = load_node(L.nodes + step_node(sj[k]));
+            na[k] = load_node(L.nodes + step_node(si[k]), pol_keep);
+            nb[k] = load_node(L.nodes + step_node(sj[k]), pol_keep);
         }
 #pragma unroll
         for (int k = 0; k < SPT; ++k) {
             if (!act[k]) continue;
-            const int64_t pa = endpoint_pos(si[k], ei[k], na[k].len);
-            const int64_t pb = endpoint_pos(sj[k], ej[k], nb[k].len);
+            const int64_t pa = endpoint_pos(si[k], ei[k]), pb = endpoint_pos(sj[k], ej[k]);
             const int64_t d = pa > pb ? pa - pb : pb - pa;
             if (d == 0) continue;
             const float xa = ei[k] ? na[k].ex : na[k].sx, ya = ei[k] ? na[k].ey : na[k].sy;
             const float xb = ej[k] ? nb[k].ex : nb[k].sx, yb = ej[k] ? nb[k].ey : nb[k].sy;
-            const float dx = __ll2float_rn((int64_t)na[k].ax - (int64_t)nb[k].ax) + (xa - xb);
-            const float dy = __ll2float_rn((int64_t)na[k].ay - (int64_t)nb[k].ay) + (ya - yb);
+            const float dx = __ll2float_rn((int64_t)si[k].ax - (int64_t)sj[k].ax) + (xa - xb);
+            const float dy = ya - yb;
             const float df = __ll2float_rn(d);
             const float t = (sqrtf(dx * dx + dy * dy) - df) / df;
             const float term = t * t;
@@ -480,8 +465,7 @@ __global__ void stress_kernel(StressLaunch L) {
 }
 
 // Sum the per-block partials in a fixed order (one block of 256 threads).
-__global__ void stress_finalize_kernel(const double* __restrict__ partials, int n,
-                                       double* __restrict__ out3) {
+__global__ void stress_finalize_kernel(const double* __restrict__ partials, int n, double* __restrict__ out3) {
     __shared__ double red[3][256];
     double s = 0.0, q = 0.0, c = 0.0;
     for (int b = threadIdx.x; b < n; b += blockDim.x) {
@@ -512,23 +496,19 @@ int grid_for(uint64_t work, int block, int sm_count, int per_sm) {
 
 }  // namespace
 
-size_t update_smem_bytes(uint32_t n_paths, uint32_t n_guide) {
-    return (size_t)(n_paths + 1) * sizeof(uint64_t) + (size_t)(kZipfTable + n_paths) * sizeof(float) +
-           (size_t)(n_guide + 1) * sizeof(uint16_t);
-}
 size_t stress_smem_bytes(uint32_t n_paths) { return 2 * (size_t)(n_paths + 1) * sizeof(uint64_t); }
 
-cudaError_t launch_pack_nodes(const uint32_t* node_len, uint32_t n, NodeRec* nodes,
-                              uint32_t* flags, int sm_count, cudaStream_t st) {
+cudaError_t launch_check_lengths(const uint32_t* node_len, uint32_t n, uint32_t* flags, int sm_count,
+                                 cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    pack_nodes_kernel<<<grid_for(n, 256, sm_count, 16), 256, 0, st>>>(node_len, n, nodes, flags);
+    check_lengths_kernel<<<grid_for(n, 256, sm_count, 16), 256, 0, st>>>(node_len, n, flags);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack_steps(const uint32_t* step_node, const uint8_t* step_rev,
-                              const int64_t* step_pos, const uint32_t* node_len, uint32_t n_nodes,
-                              const uint64_t* path_off, uint32_t n_paths, uint64_t n_steps,
-                              uint64_t* steps, uint32_t* flags, int sm_count, cudaStream_t st) {
+cudaError_t launch_pack_steps(const uint32_t* step_node, const uint8_t* step_rev, const int64_t* step_pos,
+                              const uint32_t* node_len, uint32_t n_nodes, const uint64_t* path_off,
+                              uint32_t n_paths, uint64_t n_steps, StepRec* steps, uint32_t* flags,
+                              int sm_count, cudaStream_t st) {
     if (n_steps == 0) return cudaSuccess;
     const size_t smem = (size_t)(n_paths + 1) * sizeof(uint64_t);
     cudaError_t e = cudaFuncSetAttribute(pack_steps_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -539,34 +519,43 @@ cudaError_t launch_pack_steps(const uint32_t* step_node, const uint8_t* step_rev
     return cudaGetLastError();
 }
 
-cudaError_t launch_path_extent(const uint64_t* steps, const uint64_t* path_off, const NodeRec* nodes,
-                               uint32_t n_paths, int64_t* out_nt, cudaStream_t st) {
-    path_extent_kernel<<<(n_paths + 127) / 128, 128, 0, st>>>(steps, path_off, nodes, n_paths, out_nt);
+cudaError_t launch_path_extent(const StepRec* steps, const uint64_t* path_off, uint32_t n_paths,
+                               int64_t* out_nt, cudaStream_t st) {
+    path_extent_kernel<<<(n_paths + 127) / 128, 128, 0, st>>>(steps, path_off, n_paths, out_nt);
     return cudaGetLastError();
 }
 
-cudaError_t launch_set_coords(const double* xy, NodeRec* nodes, uint32_t n, int anchored,
+cudaError_t launch_set_coords(const double* xy, NodeRec* nodes, int32_t* anchor, uint32_t n, int anchored,
                               uint32_t* flags, int sm_count, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    set_coords_kernel<<<grid_for(n, 256, sm_count, 16), 256, 0, st>>>(xy, nodes, n, anchored, flags);
+    set_coords_kernel<<<grid_for(n, 256, sm_count, 16), 256, 0, st>>>(xy, nodes, anchor, n, anchored, flags);
     return cudaGetLastError();
 }
 
-cudaError_t launch_get_coords(const NodeRec* nodes, double* xy, uint32_t n, int sm_count,
-                              cudaStream_t st) {
+cudaError_t launch_get_coords(const NodeRec* nodes, const int32_t* anchor, double* xy, uint32_t n,
+                              int sm_count, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    get_coords_kernel<<<grid_for(n, 256, sm_count, 16), 256, 0, st>>>(nodes, xy, n);
+    get_coords_kernel<<<grid_for(n, 256, sm_count, 16), 256, 0, st>>>(nodes, anchor, xy, n);
     return cudaGetLastError();
 }
 
-cudaError_t launch_rebase(NodeRec* nodes, uint32_t n, int sm_count, cudaStream_t st) {
+cudaError_t launch_rebase(NodeRec* nodes, int32_t* anchor, uint32_t n, uint32_t* changed, int sm_count,
+                          cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    rebase_kernel<<<grid_for(n, 256, sm_count, 16), 256, 0, st>>>(nodes, n);
+    rebase_kernel<<<grid_for(n, 256, sm_count, 16), 256, 0, st>>>(nodes, anchor, n, changed);
     return cudaGetLastError();
 }
 
-cudaError_t launch_zipf_setup(const uint64_t* path_off, uint32_t n_paths, float theta,
-                              float* zipf_B, float* zipf_T, cudaStream_t st) {
+cudaError_t launch_refresh_anchors(StepRec* steps, const int32_t* anchor, uint64_t n_steps,
+                                   const uint32_t* changed, int sm_count, cudaStream_t st) {
+    if (n_steps == 0) return cudaSuccess;
+    refresh_anchors_kernel<<<grid_for(n_steps, 256, sm_count, 8), 256, 0, st>>>(steps, anchor, n_steps,
+                                                                                 changed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zipf_setup(const uint64_t* path_off, uint32_t n_paths, float theta, float* zipf_B,
+                              float* zipf_T, cudaStream_t st) {
     const uint32_t n = n_paths > (uint32_t)kZipfTable ? n_paths : (uint32_t)kZipfTable;
     zipf_setup_kernel<<<(n + 127) / 128, 128, 0, st>>>(path_off, n_paths, theta, zipf_B, zipf_T);
     return cudaGetLastError();
@@ -586,7 +575,6 @@ static cudaError_t launch_update_t(const UpdateLaunch& L, cudaStream_t st) {
 // SM the register allocation must allow (1 = unconstrained).
 cudaError_t launch_update(const UpdateLaunch& L, cudaStream_t st) {
     if (L.n_updates == 0) return cudaSuccess;
-    if (L.block > 256 && L.minb > 1) return cudaErrorInvalidValue;
     switch (L.upt * 10 + L.minb) {
         case 11: return launch_update_t<1, 1>(L, st);
         case 14: return launch_update_t<1, 4>(L, st);
@@ -601,28 +589,27 @@ cudaError_t launch_update(const UpdateLaunch& L, cudaStream_t st) {
     }
 }
 
-cudaError_t launch_debug_sample(const SamplerArgs& s, uint64_t u_begin, uint64_t count,
-                                const NodeRec* nodes, void* out, int sm_count, cudaStream_t st) {
+cudaError_t launch_debug_sample(const SamplerArgs& s, uint64_t u_begin, uint64_t count, void* out,
+                                int sm_count, cudaStream_t st) {
     if (count == 0) return cudaSuccess;
     const size_t smem = update_smem_bytes(s.n_paths, s.n_guide);
     cudaError_t e = cudaFuncSetAttribute(debug_sample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    debug_sample_kernel<<<grid_for(count, 256, sm_count, 8), 256, smem, st>>>(
-        s, u_begin, count, nodes, static_cast<pgsgd_sample*>(out));
+    debug_sample_kernel<<<grid_for(count, 256, sm_count, 8), 256, smem, st>>>(s, u_begin, count,
+                                                                              static_cast<pgsgd_sample*>(out));
     return cudaGetLastError();
 }
 
-cudaError_t launch_debug_sweep(const SamplerArgs& s, uint64_t u_begin, uint64_t count,
-                               const NodeRec* nodes, float eta, float4* out, int sm_count,
-                               cudaStream_t st) {
+cudaError_t launch_debug_sweep(const SamplerArgs& s, uint64_t u_begin, uint64_t count, const NodeRec* nodes,
+                               float eta, float4* out, int sm_count, cudaStream_t st) {
     if (count == 0) return cudaSuccess;
     const size_t smem = update_smem_bytes(s.n_paths, s.n_guide);
     cudaError_t e = cudaFuncSetAttribute(debug_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    debug_sweep_kernel<<<grid_for(count, 256, sm_count, 8), 256, smem, st>>>(s, u_begin, count, nodes,
-                                                                             eta, out);
+    debug_sweep_kernel<<<grid_for(count, 256, sm_count, 8), 256, smem, st>>>(s, u_begin, count, nodes, eta,
+                                                                             out);
     return cudaGetLastError();
 }
 
