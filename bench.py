@@ -378,11 +378,15 @@ def run_e2e(pg, g, args, dev):
 
 
 def kernel_revision():
-    """Hash of the update kernel's sources: ncu traffic counts are only valid for it."""
+    """Hash of the update kernel's code (the device helpers and the update
+    kernel's section): a recorded ncu traffic count is only valid for it."""
     import hashlib
-    h = hashlib.sha1()
-    for f in ("pgsgd_kernels.cu", "pgsgd_device.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2409_00876_gb300", "csrc", f), "rb").read())
+    csrc = os.path.join(ROOT, "paper_2409_00876_gb300", "csrc")
+    h = hashlib.sha1(open(os.path.join(csrc, "pgsgd_device.cuh"), "rb").read())
+    text = open(os.path.join(csrc, "pgsgd_kernels.cu")).read()
+    a = text.find("// ---------------------------------------------------------------- update math")
+    b = text.find("// ---------------------------------------------------------------- debug kernels")
+    h.update((text[a:b] if 0 <= a < b else text).encode())
     return h.hexdigest()[:12]
 
 

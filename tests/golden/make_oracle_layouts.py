@@ -32,6 +32,12 @@ PLAN = {
 }
 
 
+def oracle_sha():
+    import hashlib
+    src = os.path.join(ROOT, "oracle", "pgsgd_oracle.c")
+    return hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+
+
 def fingerprint(g):
     return dict(n_nodes=g.n_nodes, n_paths=g.n_paths, n_steps=g.n_steps,
                 pos_sum=int(g.step_pos.sum() % (1 << 61)),
@@ -49,7 +55,8 @@ def main():
         seeds, per_step, sseed = PLAN[name]
         g = make_graph(name)
         threads = 1 if name == "tiny" else args.threads
-        entry = dict(fingerprint=fingerprint(g), iterations=30, theta=0.99, updates_per_step=10,
+        entry = dict(fingerprint=fingerprint(g), oracle_sha=oracle_sha(), iterations=30, theta=0.99,
+                     updates_per_step=10,
                      stress_samples_per_step=per_step, stress_seed=sseed, oracle_threads=threads,
                      runs=[])
         init = O.sampled_stress(g, g.init_xy, per_step=per_step, seed=sseed, n_threads=args.threads)
