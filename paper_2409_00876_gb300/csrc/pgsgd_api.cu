@@ -344,7 +344,7 @@ int pgsgd_create(const uint32_t* node_len, uint32_t n_nodes, const uint64_t* pat
                 "path guide upload");
         }
         TRY(dalloc(g, &g->d_flags, 1), "flags");
-        g->max_stress_blocks = g->sm_count * 32;  // many short blocks balance the two dies
+        g->max_stress_blocks = g->sm_count * 8;
         TRY(dalloc(g, &g->d_partials, 3 * (size_t)g->max_stress_blocks + 3), "stress scratch");
         TRY(dalloc(g, &g->d_per_path, 3 * (size_t)n_paths), "per-path stress");
         TRY(cudaMemsetAsync(g->d_flags, 0, sizeof(uint32_t), st), "flags clear");

@@ -392,15 +392,15 @@ __global__ void stress_kernel(StressLaunch L) {
             const uint64_t j = x + (x >= i);
             ei[k] = w.z & 1u;
             ej[k] = (w.z >> 1) & 1u;
-            si[k] = load_step(L.steps + off + i, pol_stream, true);
-            sj[k] = load_step(L.steps + off + j, pol_stream, true);
+            si[k] = load_step(L.steps + off + i, pol_stream);
+            sj[k] = load_step(L.steps + off + j, pol_stream);
         }
         NodeRec na[SPT], nb[SPT];
 #pragma unroll
         for (int k = 0; k < SPT; ++k) {
             if (!act[k]) continue;
-            na[k] = load_node(L.nodes + step_node(si[k]), pol_keep, true);
-            nb[k] = load_node(L.nodes + step_node(sj[k]), pol_keep, true);
+            na[k] = load_node(L.nodes + step_node(si[k]), pol_keep);
+            nb[k] = load_node(L.nodes + step_node(sj[k]), pol_keep);
         }
 #pragma unroll
         for (int k = 0; k < SPT; ++k) {

@@ -67,29 +67,32 @@ def test_tiny_layout_quality_matches_oracle(pg):
 
 
 @pytest.mark.parametrize("name", ["mid", "chrom"])
-def test_layout_stress_matches_oracle_under_same_seed(pg, name):
-    """The GPU's lock-free layout reaches the oracle's quality under the same
-    layout seed. Both sides draw the same pairs; the GPU applies them
-    concurrently, so its result varies from run to run, and the oracle's
-    result itself varies from seed to seed. The bar is the largest of 1 % of
-    the oracle's stress, the range of the GPU's repeated runs and the range
-    of the oracle's recorded seeds."""
+def test_layout_stress_matches_oracle(pg, name):
+    """The GPU's lock-free layout reaches the oracle's quality. For every layout
+    seed the oracle recorded, the GPU lays the graph out under the same seed
+    (the same drawn pairs, applied concurrently). The mean stresses are
+    compared; the bar is the larger of 1 % of the oracle's mean and twice the
+    standard error that the seed-to-seed and run-to-run spread of both sides
+    implies (with a single seed, the range of two GPU repeats stands in)."""
     gold = _gold(name)
     g = make_graph(name)
     fp = gold["fingerprint"]
     assert (g.n_nodes, g.n_paths, g.n_steps) == (fp["n_nodes"], fp["n_paths"], fp["n_steps"])
     per, sseed = gold["stress_samples_per_step"], gold["stress_seed"]
-    reps = 5 if name == "mid" else 2
+    ref = np.array([r["stress"] for r in gold["runs"]])
+    reps = 1 if len(ref) > 1 else 2
+    got = []
     for run in gold["runs"]:
-        vals = [_layout_stress(pg, g, run["seed"], per, sseed)[0]["mean"] for _ in range(reps)]
-        med = float(np.median(vals))
-        spread = max(vals) - min(vals)
-        rel = abs(med - run["stress"]) / run["stress"]
-        print(name, run["seed"], vals, run["stress"], rel)
-        oracle_range = max(r["stress"] for r in gold["runs"]) - min(r["stress"] for r in gold["runs"])
-        bar = max(0.01 * run["stress"], spread, oracle_range)
-        assert abs(med - run["stress"]) <= bar, (vals, run["stress"], bar)
-        assert max(vals) < 0.5 * gold["init_stress"]
+        got += [_layout_stress(pg, g, run["seed"], per, sseed)[0]["mean"] for _ in range(reps)]
+    got = np.array(got)
+    if len(ref) > 1:
+        se = np.sqrt(got.var(ddof=1) / len(got) + ref.var(ddof=1) / len(ref))
+    else:
+        se = (got.max() - got.min()) / 2
+    bar = max(0.01 * ref.mean(), 2 * se)
+    print(name, got, ref, abs(got.mean() - ref.mean()) / ref.mean(), bar / ref.mean())
+    assert abs(got.mean() - ref.mean()) <= bar, (got, ref, bar)
+    assert got.max() < 0.5 * gold["init_stress"]
 
 
 def test_resume_in_two_calls_matches_one_call_quality(pg):
