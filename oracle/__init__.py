@@ -79,6 +79,10 @@ def _L():
             lib.orc_sampled_stress_paths.restype = i32
             lib.orc_full_stress.argtypes = gargs + [P, P]
             lib.orc_full_stress.restype = i32
+            lib.orc_dstress.argtypes = gargs + [P, u64, u64, P]
+            lib.orc_dstress.restype = i32
+            lib.orc_dstress_grad.argtypes = gargs + [P, u64, u64, P]
+            lib.orc_dstress_grad.restype = i32
             _lib = lib
     return _lib
 
@@ -224,3 +228,21 @@ def full_stress(g, xy):
     out = np.zeros(2, dtype=np.float64)
     _L().orc_full_stress(*_ga(g).args(), _ptr(xy), _ptr(out))
     return float(out[0]), int(out[1])
+
+
+# ---------------------------------------------------------------- differentiable stress
+
+def dstress(g, xy, n_pairs, seed):
+    """Eq. 2's estimator over a fixed set of n_pairs samples: (F, n_valid)."""
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    out = np.zeros(2, dtype=np.float64)
+    _L().orc_dstress(*_ga(g).args(), _ptr(xy), int(n_pairs), int(seed), _ptr(out))
+    return float(out[0]), int(out[1])
+
+
+def dstress_grad(g, xy, n_pairs, seed):
+    """dF/d(sx, sy, ex, ey) of dstress, [n_nodes, 4] float64."""
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    grad = np.zeros_like(xy)
+    _L().orc_dstress_grad(*_ga(g).args(), _ptr(xy), int(n_pairs), int(seed), _ptr(grad))
+    return grad

@@ -735,3 +735,97 @@ int orc_full_stress(GRAPH_ARGS, const double *xy, double *out)
     out[1] = pairs;
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Differentiable sampled stress: Eq. 2's estimator over a fixed set of */
+/* n_pairs samples, sample q drawn by counter (q_lo, q_hi, 0xC0000000,  */
+/* 0): the global step g (path in proportion to |p|, step i uniform),  */
+/* the partner j uniform among the path's other steps from w3 and the  */
+/* upper 28 bits of w2, endpoint coins bits 0 and 1 of w2. Samples on   */
+/* paths with fewer than two steps or with d_ref = 0 are left out.      */
+/* F = (1 / n_valid) sum ((|v_i - v_j| - d) / d)^2, and its gradient    */
+/* dF/dv_i = (2 / n_valid) t (v_i - v_j) / (d |v_i - v_j|), dF/dv_j =   */
+/* -dF/dv_i with t = (|v_i - v_j| - d) / d (zero where |v_i - v_j| = 0).*/
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int valid;
+    uint32_t ni, nj;
+    int ei, ej;
+    int64_t d;
+} dpair_t;
+
+static void dstress_pair(const orc_graph *G, uint64_t seed, uint64_t q, dpair_t *r)
+{
+    uint32_t w[4];
+    philox_block(seed, (uint32_t)q, (uint32_t)(q >> 32), 0xC0000000u, 0u, w);
+    uint64_t steps = G->path_off[G->n_paths];
+    uint64_t g = mulhi64((uint64_t)w[0] | ((uint64_t)w[1] << 32), steps);
+    uint32_t p = find_path(G, g);
+    uint64_t off = G->path_off[p], n = G->path_off[p + 1] - off;
+    r->valid = 0;
+    if (n < 2) return;
+    uint64_t i = g - off;
+    uint64_t x = mulhi64(((uint64_t)w[3] << 32) | (w[2] & ~15u), n - 1);
+    uint64_t j = x + (x >= i);
+    r->ei = w[2] & 1u;
+    r->ej = (w[2] >> 1) & 1u;
+    int64_t a = endpoint_pos(G, off + i, r->ei), b = endpoint_pos(G, off + j, r->ej);
+    r->d = a > b ? a - b : b - a;
+    if (r->d == 0) return;
+    r->ni = G->step_node[off + i];
+    r->nj = G->step_node[off + j];
+    r->valid = 1;
+}
+
+/* out = {F, n_valid} */
+int orc_dstress(GRAPH_ARGS, const double *xy, uint64_t n_pairs, uint64_t seed, double *out)
+{
+    GRAPH_INIT;
+    double sum = 0.0, cnt = 0.0;
+    for (uint64_t q = 0; q < n_pairs; ++q) {
+        dpair_t r;
+        dstress_pair(&G, seed, q, &r);
+        if (!r.valid) continue;
+        double dx = xy[4 * (uint64_t)r.ni + 2 * r.ei] - xy[4 * (uint64_t)r.nj + 2 * r.ej];
+        double dy = xy[4 * (uint64_t)r.ni + 2 * r.ei + 1] - xy[4 * (uint64_t)r.nj + 2 * r.ej + 1];
+        double t = (sqrt(dx * dx + dy * dy) - (double)r.d) / (double)r.d;
+        sum += t * t;
+        cnt += 1.0;
+    }
+    out[0] = cnt > 0 ? sum / cnt : 0.0;
+    out[1] = cnt;
+    return 0;
+}
+
+/* grad[n_nodes][4] = dF / d(sx, sy, ex, ey) */
+int orc_dstress_grad(GRAPH_ARGS, const double *xy, uint64_t n_pairs, uint64_t seed, double *grad)
+{
+    GRAPH_INIT;
+    memset(grad, 0, 4 * (size_t)n_nodes * sizeof(double));
+    double cnt = 0.0;
+    for (uint64_t q = 0; q < n_pairs; ++q) {
+        dpair_t r;
+        dstress_pair(&G, seed, q, &r);
+        if (r.valid) cnt += 1.0;
+    }
+    if (cnt == 0.0) return 0;
+    for (uint64_t q = 0; q < n_pairs; ++q) {
+        dpair_t r;
+        dstress_pair(&G, seed, q, &r);
+        if (!r.valid) continue;
+        double *vi = (double *)xy + 4 * (uint64_t)r.ni + 2 * r.ei;
+        double *vj = (double *)xy + 4 * (uint64_t)r.nj + 2 * r.ej;
+        double dx = vi[0] - vj[0], dy = vi[1] - vj[1];
+        double mag = sqrt(dx * dx + dy * dy);
+        if (mag == 0.0) continue;
+        double d = (double)r.d;
+        double t = (mag - d) / d;
+        double c = 2.0 * t / (d * mag) / cnt;
+        grad[4 * (uint64_t)r.ni + 2 * r.ei] += c * dx;
+        grad[4 * (uint64_t)r.ni + 2 * r.ei + 1] += c * dy;
+        grad[4 * (uint64_t)r.nj + 2 * r.ej] -= c * dx;
+        grad[4 * (uint64_t)r.nj + 2 * r.ej + 1] -= c * dy;
+    }
+    return 0;
+}
