@@ -241,6 +241,40 @@ int pgsgd_debug_sweep(pgsgd_graph *g, uint32_t t, uint32_t iter_max, double eta,
                       float *out, void *cuda_stream);
 
 /*
+ * Differentiable sampled path stress. F is Eq. 2's estimator (Section VI-B)
+ * over a fixed set of n_pairs samples (sample q: Philox counter
+ * (q_lo, q_hi, 0xC0000000, 0) under `seed`; path in proportion to |p|, step
+ * i uniform, partner j uniform among the other steps, a coin per endpoint;
+ * samples with d_ref = 0 or on paths of fewer than two steps are left out):
+ *   F = (1 / n_valid) sum_q ((|v_i - v_j| - d) / d)^2
+ * pgsgd_dstress writes F and n_valid (host). Synchronous.
+ */
+int pgsgd_dstress(pgsgd_graph *g, uint64_t n_pairs, uint64_t seed, double *value,
+                  uint64_t *n_valid, void *cuda_stream);
+
+/*
+ * Hand-written backward of the same objective: grad[n_nodes][4] (float32,
+ * DEVICE memory, overwritten) = scale * sum_q d(t_q^2)/d(sx, sy, ex, ey),
+ * t_q = (|v_i - v_j| - d) / d; pass scale = (upstream gradient) / n_valid
+ * for dF. Contributions are added with vector atomics (order not fixed).
+ * Asynchronous on the stream.
+ */
+int pgsgd_dstress_backward(pgsgd_graph *g, uint64_t n_pairs, uint64_t seed, double scale,
+                           float *grad, void *cuda_stream);
+
+/*
+ * Gradient of the single-pair stress ((|v_i - v_j| - d) / d)^2 (Algorithm 1,
+ * line 14) of every update u in [u_begin, u_begin + count) of iteration t,
+ * at the current layout: out[count][4] float32 (host) =
+ * (d/dx_i, d/dy_i, d/dx_j, d/dy_j); zeros where the update is skipped.
+ * Together with pgsgd_debug_sweep it shows each move equals
+ * -(eta / 4) times this gradient while eta / d^2 < 1. Synchronous.
+ */
+int pgsgd_debug_pair_grad(pgsgd_graph *g, uint32_t t, uint32_t iter_max, double theta,
+                          uint64_t seed, uint64_t u_begin, uint64_t count, float *out,
+                          void *cuda_stream);
+
+/*
  * Update-kernel timing (PGSGD_OPT_TIMING = 1): total milliseconds of all
  * update-kernel launches since the last reset, measured with CUDA events on
  * the launching stream, the number of launches and the updates they ran.

@@ -54,6 +54,15 @@ def _arg(x, dtype):
     return a.ctypes.data_as(C.c_void_p), 0, a
 
 
+def _arg_f32(x):
+    if not _is_torch(x):
+        raise TypeError("expected a torch tensor")
+    import torch
+    if x.dtype != torch.float32 or not x.is_contiguous():
+        raise TypeError("expected a contiguous float32 tensor")
+    return C.c_void_p(x.data_ptr()), int(x.is_cuda), x
+
+
 class Graph:
     """A pangenome graph resident on the current CUDA device.
 
@@ -174,6 +183,31 @@ class Graph:
                                             int(seed), int(u_begin), int(count),
                                             out.ctypes.data_as(C.c_void_p),
                                             stream or _current_stream()))
+        return out
+
+    def dstress(self, n_pairs, seed, stream=None):
+        """Differentiable sampled stress: (value, n_valid)."""
+        v = C.c_double()
+        n = C.c_uint64()
+        N.check(self._lib.pgsgd_dstress(self._h, int(n_pairs), int(seed), C.byref(v), C.byref(n),
+                                        stream or _current_stream()))
+        return v.value, n.value
+
+    def dstress_backward(self, n_pairs, seed, scale, grad, stream=None):
+        """grad (float32 CUDA tensor [n_nodes, 4]) <- scale * sum of per-sample gradients."""
+        p, dev, keep = _arg_f32(grad)
+        if not dev:
+            raise ValueError("grad must be a CUDA tensor")
+        N.check(self._lib.pgsgd_dstress_backward(self._h, int(n_pairs), int(seed), float(scale), p,
+                                                 stream or _current_stream()))
+        return grad
+
+    def debug_pair_grad(self, t, iter_max, theta, seed, u_begin, count, stream=None):
+        out = np.zeros((count, 4), dtype=np.float32)
+        N.check(self._lib.pgsgd_debug_pair_grad(self._h, t, iter_max, float(theta), int(seed),
+                                                int(u_begin), int(count),
+                                                out.ctypes.data_as(C.c_void_p),
+                                                stream or _current_stream()))
         return out
 
     def timing_read(self, reset=True):

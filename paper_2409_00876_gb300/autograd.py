@@ -1,0 +1,54 @@
+"""Sampled path stress as a differentiable PyTorch function.
+
+``sampled_stress(xy, graph, n_pairs, seed)`` returns the estimator of Eq. 2
+over a fixed sample set as a scalar tensor whose gradient with respect to the
+layout ``xy`` (float64 CUDA tensor [n_nodes, 4]) comes from the library's
+hand-written backward kernel. The graph object only holds the path data; the
+layout passed in is the one differentiated.
+"""
+from __future__ import annotations
+
+import torch
+
+
+class SampledStress(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, xy, graph, n_pairs, seed):
+        graph.set_coords(xy.detach())
+        value, n_valid = graph.dstress(n_pairs, seed)
+        ctx.graph = graph
+        ctx.n_pairs = n_pairs
+        ctx.seed = seed
+        ctx.n_valid = n_valid
+        ctx.save_for_backward(xy.detach())
+        return torch.tensor(value, dtype=torch.float64, device=xy.device)
+
+    @staticmethod
+    def backward(ctx, gout):
+        (xy,) = ctx.saved_tensors
+        graph = ctx.graph
+        graph.set_coords(xy)
+        grad = torch.empty(xy.shape, dtype=torch.float32, device=xy.device)
+        scale = float(gout) / max(ctx.n_valid, 1)
+        graph.dstress_backward(ctx.n_pairs, ctx.seed, scale, grad)
+        return grad.to(torch.float64), None, None, None
+
+
+def sampled_stress(xy, graph, n_pairs=10_000_000, seed=1):
+    return SampledStress.apply(xy, graph, n_pairs, seed)
+
+
+def refine(graph, xy, steps=200, lr=0.05, n_pairs=10_000_000, seed=1, eval_fn=None):
+    """Full-batch gradient refinement of a layout with Adam on the
+    differentiable sampled stress. Returns the refined layout and the
+    objective's trace (first and last values, and eval_fn's if given)."""
+    x = xy.detach().clone().requires_grad_(True)
+    opt = torch.optim.Adam([x], lr=lr)
+    trace = []
+    for _ in range(steps):
+        opt.zero_grad()
+        f = sampled_stress(x, graph, n_pairs, seed)
+        f.backward()
+        opt.step()
+        trace.append(float(f.detach()))
+    return x.detach(), trace

@@ -741,4 +741,60 @@ int pgsgd_debug_sweep(pgsgd_graph* g, uint32_t t, uint32_t iter_max, double eta,
     return PGSGD_OK;
 }
 
+int pgsgd_dstress(pgsgd_graph* g, uint64_t n_pairs, uint64_t seed, double* value, uint64_t* n_valid,
+                  void* cuda_stream) {
+    if (!g || !value) return fail(PGSGD_EINVAL, "NULL argument");
+    if (!g->has_coords) return fail(PGSGD_EINVAL, "no layout: call pgsgd_set_coords first");
+    cudaStream_t st = S(cuda_stream);
+    int rc = ensure_zipf(g, 0.99f, st);
+    if (rc) return rc;
+    const SamplerArgs a = sampler_args(g, 1, 0, 0.99f, seed);
+    const uint64_t want = (n_pairs + 255) / 256;
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)g->max_stress_blocks));
+    CK(launch_dstress_forward(a, g->d_nodes, n_pairs, g->d_partials, grid, st), "dstress forward");
+    double* tot = g->d_partials + 3 * (size_t)g->max_stress_blocks;
+    CK(launch_stress_finalize(g->d_partials, grid, tot, st), "dstress finalize");
+    double h[3];
+    CK(cudaMemcpyAsync(h, tot, sizeof h, cudaMemcpyDeviceToHost, st), "dstress readback");
+    CK(cudaStreamSynchronize(st), "dstress sync");
+    *value = h[2] > 0 ? h[0] / h[2] : 0.0;
+    if (n_valid) *n_valid = (uint64_t)h[2];
+    return PGSGD_OK;
+}
+
+int pgsgd_dstress_backward(pgsgd_graph* g, uint64_t n_pairs, uint64_t seed, double scale, float* grad,
+                           void* cuda_stream) {
+    if (!g || !grad) return fail(PGSGD_EINVAL, "NULL argument");
+    if (!g->has_coords) return fail(PGSGD_EINVAL, "no layout: call pgsgd_set_coords first");
+    cudaStream_t st = S(cuda_stream);
+    int rc = ensure_zipf(g, 0.99f, st);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(grad, 0, (size_t)g->n_nodes * 4 * sizeof(float), st), "gradient clear");
+    CK(launch_dstress_backward(sampler_args(g, 1, 0, 0.99f, seed), g->d_nodes, n_pairs, (float)scale, grad,
+                               g->sm_count, st),
+       "dstress backward");
+    return PGSGD_OK;
+}
+
+int pgsgd_debug_pair_grad(pgsgd_graph* g, uint32_t t, uint32_t iter_max, double theta, uint64_t seed,
+                          uint64_t u_begin, uint64_t count, float* out, void* cuda_stream) {
+    if (!g || (!out && count)) return fail(PGSGD_EINVAL, "NULL argument");
+    if (!g->has_coords) return fail(PGSGD_EINVAL, "no layout: call pgsgd_set_coords first");
+    if (iter_max == 0 || t >= iter_max) return fail(PGSGD_EINVAL, "need t < iter_max");
+    int rc = check_theta(theta);
+    if (rc) return rc;
+    if (count == 0) return PGSGD_OK;
+    cudaStream_t st = S(cuda_stream);
+    rc = ensure_zipf(g, (float)theta, st);
+    if (rc) return rc;
+    rc = ensure_debug(g, count * sizeof(float4));
+    if (rc) return rc;
+    CK(launch_pair_grad(sampler_args(g, iter_max, t, (float)theta, seed), u_begin, count, g->d_nodes,
+                        static_cast<float4*>(g->d_debug), g->sm_count, st),
+       "pair gradient");
+    CK(cudaMemcpyAsync(out, g->d_debug, count * sizeof(float4), cudaMemcpyDeviceToHost, st), "pair grad readback");
+    CK(cudaStreamSynchronize(st), "pair grad sync");
+    return PGSGD_OK;
+}
+
 }  // extern "C"

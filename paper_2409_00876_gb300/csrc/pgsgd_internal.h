@@ -81,6 +81,13 @@ cudaError_t launch_debug_sweep(const SamplerArgs& s, uint64_t u_begin, uint64_t 
 cudaError_t launch_stress(const StressLaunch& L, cudaStream_t st);
 cudaError_t launch_stress_finalize(const double* partials, int n, double* out3, cudaStream_t st);
 
+cudaError_t launch_dstress_forward(const SamplerArgs& s, const NodeRec* nodes, uint64_t n_pairs, double* partials,
+                                   int grid, cudaStream_t st);
+cudaError_t launch_dstress_backward(const SamplerArgs& s, const NodeRec* nodes, uint64_t n_pairs, float scale,
+                                    float* grad, int sm_count, cudaStream_t st);
+cudaError_t launch_pair_grad(const SamplerArgs& s, uint64_t u_begin, uint64_t count, const NodeRec* nodes,
+                             float4* out, int sm_count, cudaStream_t st);
+
 // Record the calling thread's error message (read by pgsgd_last_error) and
 // return status.
 int report_error(int status, const char* fmt, ...);

@@ -165,55 +165,9 @@ __global__ void zipf_setup_kernel(const uint64_t* __restrict__ path_off, uint32_
     if (p < (uint32_t)kZipfTable) out_T[p] = p == 0 ? 0.0f : zipf_threshold(p, omt, theta);
 }
 
-// Stage the path table, the guide and the per-theta Zipf tables in shared memory.
-__device__ __forceinline__ PathTable stage_paths(const SamplerArgs& a, unsigned char* smem,
-                                                 ZipfConsts& zc_shared) {
-    uint64_t* s_off = reinterpret_cast<uint64_t*>(smem);
-    float* s_T = reinterpret_cast<float*>(s_off + a.n_paths + 1);
-    float* s_B = s_T + kZipfTable;
-    uint16_t* s_guide = reinterpret_cast<uint16_t*>(s_B + a.n_paths);
-    for (uint32_t k = threadIdx.x; k <= a.n_paths; k += blockDim.x) s_off[k] = a.path_off[k];
-    for (uint32_t k = threadIdx.x; k < a.n_paths; k += blockDim.x) s_B[k] = a.zipf_B[k];
-    for (uint32_t k = threadIdx.x; k < (uint32_t)kZipfTable; k += blockDim.x) s_T[k] = a.zipf_T[k];
-    for (uint32_t k = threadIdx.x; k <= a.n_guide; k += blockDim.x) s_guide[k] = a.guide[k];
-    if (threadIdx.x == 0) {
-        ZipfConsts z;
-        z.theta = a.zc.theta;
-        zipf_theta_consts(z.theta, z.omt, z.A, z.s);
-        zc_shared = z;
-    }
-    __syncthreads();
-    return PathTable{s_off, s_B, s_T, s_guide, a.n_paths, a.guide_shift};
-}
-
 // ---------------------------------------------------------------- update math
 
-struct Move {
-    float dxi, dyi, dxj, dyj;  // change of v_i and v_j
-    bool moved;
-};
-
-// The update of Zheng et al. that Algorithm 1, line 15 applies (Fig. 3):
-// w = d^-2, mu = min(eta w, 1), r = mu (|v_i - v_j| - d) / (2 |v_i - v_j|),
-// v_i -= r (v_i - v_j), v_j += r (v_i - v_j). FP32; x anchors differenced in
-// integers so chromosome-scale coordinates keep their resolution.
-__device__ __forceinline__ Move pair_move(const NodeRec& a, int32_t axa, uint32_t ea, const NodeRec& b,
-                                          int32_t axb, uint32_t eb, int64_t d, float eta) {
-    Move m;
-    const float xa = ea ? a.ex : a.sx, ya = ea ? a.ey : a.sy;
-    const float xb = eb ? b.ex : b.sx, yb = eb ? b.ey : b.sy;
-    const float dx = __ll2float_rn((int64_t)axa - (int64_t)axb) + (xa - xb);
-    const float dy = ya - yb;
-    const float mag = sqrtf(dx * dx + dy * dy);
-    m.moved = mag > 0.0f;
-    const float df = __ll2float_rn(d);
-    const float w = 1.0f / (df * df);
-    const float mu = fminf(eta * w, 1.0f);
-    const float r = m.moved ? mu * (mag - df) / (2.0f * mag) : 0.0f;
-    const float rx = r * dx, ry = r * dy;
-    m.dxi = -rx; m.dyi = -ry; m.dxj = rx; m.dyj = ry;
-    return m;
-}
+// (stage_paths and pair_move live in pgsgd_device.cuh)
 
 // ---------------------------------------------------------------- the update kernel
 
