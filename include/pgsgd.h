@@ -241,6 +241,17 @@ int pgsgd_debug_sweep(pgsgd_graph *g, uint32_t t, uint32_t iter_max, double eta,
                       float *out, void *cuda_stream);
 
 /*
+ * Path stress (Eq. 1, Section VI-A) of the current layout: for every path and
+ * every pair of distinct steps i < j, the mean of ((|v_i - v_j| - d) / d)^2
+ * over the four endpoint combinations with d_ref > 0, averaged over the pairs
+ * with at least one such combination (value, host) and their number
+ * (n_pairs, host, optional). FP32 terms, FP64 sums. Work grows as
+ * sum_p |p|^2: meant for small graphs and for checking the sampled metric.
+ * Synchronous.
+ */
+int pgsgd_full_stress(pgsgd_graph *g, double *value, uint64_t *n_pairs, void *cuda_stream);
+
+/*
  * Differentiable sampled path stress. F is Eq. 2's estimator (Section VI-B)
  * over a fixed set of n_pairs samples (sample q: Philox counter
  * (q_lo, q_hi, 0xC0000000, 0) under `seed`; path in proportion to |p|, step

@@ -185,6 +185,13 @@ class Graph:
                                             stream or _current_stream()))
         return out
 
+    def full_stress(self, stream=None):
+        """Eq. 1 over all same-path step pairs: (value, number of pairs)."""
+        v = C.c_double()
+        n = C.c_uint64()
+        N.check(self._lib.pgsgd_full_stress(self._h, C.byref(v), C.byref(n), stream or _current_stream()))
+        return v.value, n.value
+
     def dstress(self, n_pairs, seed, stream=None):
         """Differentiable sampled stress: (value, n_valid)."""
         v = C.c_double()

@@ -53,6 +53,7 @@ _SIGS = {
     "pgsgd_timing_read": ([P, P, P, P, i32], i32),
     "pgsgd_stress_noalloc": ([P, u32, P, u32, P, P, P, P, u32, u64, P, P], i32),
     "pgsgd_dstress": ([P, u64, u64, P, P, P], i32),
+    "pgsgd_full_stress": ([P, P, P, P], i32),
     "pgsgd_dstress_backward": ([P, u64, u64, dbl, P, P], i32),
     "pgsgd_debug_pair_grad": ([P, u32, u32, dbl, u64, u64, u64, P, P], i32),
     "pgsgd_last_error": ([], C.c_char_p),

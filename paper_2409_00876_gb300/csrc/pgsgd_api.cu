@@ -797,4 +797,21 @@ int pgsgd_debug_pair_grad(pgsgd_graph* g, uint32_t t, uint32_t iter_max, double 
     return PGSGD_OK;
 }
 
+int pgsgd_full_stress(pgsgd_graph* g, double* value, uint64_t* n_pairs, void* cuda_stream) {
+    if (!g || !value) return fail(PGSGD_EINVAL, "NULL argument");
+    if (!g->has_coords) return fail(PGSGD_EINVAL, "no layout: call pgsgd_set_coords first");
+    cudaStream_t st = S(cuda_stream);
+    const int grid = g->max_stress_blocks;
+    CK(launch_full_stress(g->d_steps, g->d_nodes, g->d_path_off, g->n_paths, g->n_steps, g->d_partials, grid, st),
+       "full stress");
+    double* tot = g->d_partials + 3 * (size_t)g->max_stress_blocks;
+    CK(launch_stress_finalize(g->d_partials, grid, tot, st), "full stress finalize");
+    double h[3];
+    CK(cudaMemcpyAsync(h, tot, sizeof h, cudaMemcpyDeviceToHost, st), "full stress readback");
+    CK(cudaStreamSynchronize(st), "full stress sync");
+    *value = h[2] > 0 ? h[0] / h[2] : 0.0;
+    if (n_pairs) *n_pairs = (uint64_t)h[2];
+    return PGSGD_OK;
+}
+
 }  // extern "C"

@@ -88,6 +88,9 @@ cudaError_t launch_dstress_backward(const SamplerArgs& s, const NodeRec* nodes, 
 cudaError_t launch_pair_grad(const SamplerArgs& s, uint64_t u_begin, uint64_t count, const NodeRec* nodes,
                              float4* out, int sm_count, cudaStream_t st);
 
+cudaError_t launch_full_stress(const StepRec* steps, const NodeRec* nodes, const uint64_t* path_off, uint32_t P,
+                               uint64_t S, double* partials, int grid, cudaStream_t st);
+
 // Record the calling thread's error message (read by pgsgd_last_error) and
 // return status.
 int report_error(int status, const char* fmt, ...);
