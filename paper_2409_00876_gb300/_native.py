@@ -21,6 +21,10 @@ OPT = dict(coord_mode=1, updates_per_step=2, block=3, blocks_per_sm=4, updates_p
            min_blocks=10, l2_fetch=11, store_mode=12, l2_hints=13, prefetch64=14)
 
 
+BOPT = dict(mode=1, cuda_graph=2, block=3, updates_per_thread=4, chunk=5, max_concurrent=6,
+            updates_per_step=7, timeout_ms=8, timing=9, stall_test=10, blocks_per_sm=11)
+
+
 class StressResult(C.Structure):
     _fields_ = [("mean", dbl), ("stddev", dbl), ("ci_lo", dbl), ("ci_hi", dbl),
                 ("n_valid", u64), ("n_skipped", u64)]
@@ -30,6 +34,12 @@ class Info(C.Structure):
     _fields_ = [("n_steps", u64), ("device_bytes", u64), ("max_path_steps", u64),
                 ("max_path_nt", i64), ("n_nodes", u32), ("n_paths", u32), ("device", C.c_int32),
                 ("sm_count", C.c_int32)]
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("n_steps", u64), ("device_bytes", u64), ("last_launches", u64), ("n_graphs", u32),
+                ("n_nodes", u32), ("n_paths", u32), ("max_graph_paths", u32), ("last_grid", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class PgsgdError(RuntimeError):
@@ -56,6 +66,18 @@ _SIGS = {
     "pgsgd_full_stress": ([P, P, P, P], i32),
     "pgsgd_dstress_backward": ([P, u64, u64, dbl, P, P], i32),
     "pgsgd_debug_pair_grad": ([P, u32, u32, dbl, u64, u64, u64, P, P], i32),
+    "pgsgd_batch_create": ([u32, P, P, P, P, P, P, P, i32, P, P], i32),
+    "pgsgd_batch_destroy": ([P], i32),
+    "pgsgd_batch_set_option": ([P, i32, i64], i32),
+    "pgsgd_batch_get_option": ([P, i32, P], i32),
+    "pgsgd_batch_info_get": ([P, P], i32),
+    "pgsgd_batch_set_coords": ([P, P, i32, P], i32),
+    "pgsgd_batch_get_coords": ([P, P, i32, P], i32),
+    "pgsgd_batch_layout": ([P, u32, P, dbl, P, u32, u32, P], i32),
+    "pgsgd_batch_stress": ([P, u32, u64, P, P], i32),
+    "pgsgd_batch_debug_sample": ([P, u32, u32, u32, dbl, u64, u64, u64, P, P], i32),
+    "pgsgd_batch_timing_read": ([P, P, P, P, i32], i32),
+    "pgsgd_batch_plan": ([u32, P, P, i32, i32, u64, i64, P, P, P], i32),
     "pgsgd_last_error": ([], C.c_char_p),
     "pgsgd_status_string": ([i32], C.c_char_p),
 }
@@ -92,9 +114,14 @@ def check(status: int):
 
 
 def declared_symbols(header: str | None = None):
-    """Function names the public header declares."""
+    """Function names the public headers (all of include/*.h, or one) declare."""
     if header is None:
-        header = os.path.join(_build.ROOT, "include", "pgsgd.h")
-    text = open(header).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(pgsgd_[a-z_]+)\s*\(", text)))
+        inc = os.path.join(_build.ROOT, "include")
+        headers = sorted(os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h"))
+    else:
+        headers = [header]
+    names = set()
+    for h in headers:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names.update(re.findall(r"\b(pgsgd_[a-z_]+)\s*\(", text))
+    return sorted(names)

@@ -15,7 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpgsgd.so")
-SOURCES = ["pgsgd_kernels.cu", "pgsgd_api.cu", "pgsgd_noalloc.cu", "pgsgd_grad.cu", "pgsgd_full.cu"]
+SOURCES = ["pgsgd_kernels.cu", "pgsgd_api.cu", "pgsgd_noalloc.cu", "pgsgd_grad.cu", "pgsgd_full.cu",
+           "pgsgd_batch.cu"]
 HEADERS = ["pgsgd_device.cuh", "pgsgd_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
@@ -33,6 +34,7 @@ def nvcc() -> str:
 def _inputs():
     files = [os.path.join(CSRC, s) for s in SOURCES + HEADERS]
     files.append(os.path.join(ROOT, "include", "pgsgd.h"))
+    files.append(os.path.join(ROOT, "include", "pgsgd_batch.h"))
     files.append(os.path.abspath(__file__))
     return files
 

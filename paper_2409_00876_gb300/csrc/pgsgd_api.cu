@@ -15,61 +15,6 @@
 
 using namespace pgsgd;
 
-struct pgsgd_graph {
-    int device = 0;
-    int sm_count = 0;
-    uint32_t n_nodes = 0, n_paths = 0;
-    uint64_t n_steps = 0;
-    uint64_t max_path_steps = 0;
-    int64_t max_path_nt = 0;
-    std::vector<uint64_t> h_path_off;
-
-    NodeRec* d_nodes = nullptr;
-    int32_t* d_anchor = nullptr;       // [V] x anchors (master copy)
-    StepRec* d_steps = nullptr;
-    uint64_t* d_path_off = nullptr;
-    uint64_t* d_sample_off = nullptr;  // stress sample offsets [P + 1]
-    float* d_zipf_B = nullptr;
-    float* d_zipf_T = nullptr;         // [kZipfTable] acceptance thresholds
-    uint16_t* d_guide = nullptr;       // [n_guide + 1]
-    uint32_t n_guide = 1, guide_shift = 0;
-    uint32_t* d_flags = nullptr;
-    uint32_t* d_changed = nullptr;     // set by a rebase that moved an anchor
-    double* d_partials = nullptr;      // stress scratch [max_stress_blocks][3] + 3 totals
-    double* d_per_path = nullptr;      // [P][3]
-    double* d_xy = nullptr;            // coordinate staging [V][4]
-    void* d_debug = nullptr;           // debug output staging
-    size_t debug_bytes = 0;
-    int max_stress_blocks = 0;
-    uint64_t stress_samples_per_step = 0;
-
-    bool has_coords = false;
-    float zipf_theta = NAN;
-
-    // options
-    int coord_mode = 0;
-    int updates_per_step = 10;
-    int block = 256;
-    int blocks_per_sm = 32;
-    int upt = 2;
-    int atomic = 0;
-    int rebase = 1;
-    int timing = 0;
-    int64_t max_concurrent = -1;  // -1 = automatic
-    int min_blocks = 1;
-    int l2_fetch = 0;
-    int store_mode = 1;  // 64-bit atomic exchange: measured fastest replace-store
-    int l2_hints = 1;
-    int pf64 = 3;
-
-    // timing
-    std::vector<cudaEvent_t> ev_free;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
-    double timing_ms = 0.0;
-    uint64_t timing_launches = 0, timing_updates = 0;
-
-    uint64_t device_bytes = 0;
-};
 
 namespace {
 
@@ -120,7 +65,9 @@ cudaError_t dalloc(pgsgd_graph* g, T** p, size_t count) {
     return e;
 }
 
-void free_graph(pgsgd_graph* g) {
+}  // namespace
+
+void pgsgd::free_graph(pgsgd_graph* g) {
     if (!g) return;
     int prev = -1;
     cudaGetDevice(&prev);
@@ -148,6 +95,8 @@ void free_graph(pgsgd_graph* g) {
     delete g;
 }
 
+namespace {
+
 const char* flag_text(uint32_t f) {
     if (f & FLAG_BAD_NODE) return "a step's node id is >= n_nodes";
     if (f & FLAG_BAD_REV) return "a step's orientation is not 0 or 1";
@@ -174,12 +123,16 @@ int check_flags(pgsgd_graph* g, cudaStream_t st, const char* what) {
     return PGSGD_OK;
 }
 
-int ensure_zipf(pgsgd_graph* g, float theta, cudaStream_t st) {
+}  // namespace
+
+int pgsgd::ensure_zipf(pgsgd_graph* g, float theta, cudaStream_t st) {
     if (g->zipf_theta == theta) return PGSGD_OK;
     CK(launch_zipf_setup(g->d_path_off, g->n_paths, theta, g->d_zipf_B, g->d_zipf_T, st), "zipf setup");
     g->zipf_theta = theta;
     return PGSGD_OK;
 }
+
+namespace {
 
 SamplerArgs sampler_args(const pgsgd_graph* g, uint32_t T, uint32_t t, float theta, uint64_t seed) {
     SamplerArgs a;
@@ -253,6 +206,15 @@ const char* pgsgd_status_string(int status) {
 int pgsgd_create(const uint32_t* node_len, uint32_t n_nodes, const uint64_t* path_off,
                  uint32_t n_paths, const uint32_t* step_node, const uint8_t* step_rev,
                  const int64_t* step_pos, int on_device, void* cuda_stream, pgsgd_graph** out) {
+    return pgsgd::graph_create(node_len, n_nodes, path_off, n_paths, step_node, step_rev, step_pos, on_device,
+                               cuda_stream, false, out);
+}
+
+}  // extern "C"
+
+int pgsgd::graph_create(const uint32_t* node_len, uint32_t n_nodes, const uint64_t* path_off, uint32_t n_paths,
+                        const uint32_t* step_node, const uint8_t* step_rev, const int64_t* step_pos, int on_device,
+                        void* cuda_stream, bool batch, pgsgd_graph** out) {
     g_last_error.clear();
     if (!out) return fail(PGSGD_EINVAL, "out is NULL");
     *out = nullptr;
@@ -260,7 +222,8 @@ int pgsgd_create(const uint32_t* node_len, uint32_t n_nodes, const uint64_t* pat
     if (n_nodes == 0) return fail(PGSGD_EINVAL, "n_nodes is 0");
     if (n_nodes >= (1u << 31)) return fail(PGSGD_ERANGE, "n_nodes %u >= 2^31", n_nodes);
     if (n_paths == 0) return fail(PGSGD_EINVAL, "n_paths is 0");
-    if (n_paths > kMaxPaths) return fail(PGSGD_ERANGE, "n_paths %u > %u", n_paths, kMaxPaths);
+    const uint32_t max_paths = batch ? kMaxBatchPaths : kMaxPaths;
+    if (n_paths > max_paths) return fail(PGSGD_ERANGE, "n_paths %u > %u", n_paths, max_paths);
     if (on_device != 0 && on_device != 1) return fail(PGSGD_EINVAL, "on_device must be 0 or 1");
     cudaStream_t st = S(cuda_stream);
 
@@ -320,7 +283,7 @@ int pgsgd_create(const uint32_t* node_len, uint32_t n_nodes, const uint64_t* pat
         TRY(dalloc(g, &g->d_sample_off, n_paths + 1), "stress sample table");
         TRY(dalloc(g, &g->d_zipf_B, n_paths), "zipf table");
         TRY(dalloc(g, &g->d_zipf_T, kZipfTable), "zipf thresholds");
-        {
+        if (!batch) {
             // guide: buckets of 2^shift steps, at most kGuideBuckets of them;
             // guide[b] = path holding step b << shift, guide[n] = P - 1
             uint32_t shift = 0;
@@ -383,6 +346,7 @@ int pgsgd_create(const uint32_t* node_len, uint32_t n_nodes, const uint64_t* pat
         TRY(cudaMemcpyAsync(nt.data(), d_nt, (size_t)n_paths * 8, cudaMemcpyDeviceToHost, st), "extent readback");
         TRY(cudaStreamSynchronize(st), "create sync");
         for (int64_t v : nt) g->max_path_nt = std::max(g->max_path_nt, v);
+        g->h_path_nt = nt;
 #undef TRY
     } while (0);
     cudaFree(t_len);
@@ -398,6 +362,8 @@ int pgsgd_create(const uint32_t* node_len, uint32_t n_nodes, const uint64_t* pat
     *out = g;
     return PGSGD_OK;
 }
+
+extern "C" {
 
 int pgsgd_destroy(pgsgd_graph* g) {
     free_graph(g);

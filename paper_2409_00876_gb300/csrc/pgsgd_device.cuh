@@ -328,6 +328,34 @@ struct Pair {
     uint32_t short_path;  // 1 = path has < 2 steps: no update
 };
 
+// Partner step j of step i in a path of n >= 2 steps (Algorithm 1, lines
+// 6-11) from the coin word w2 and the word w3 of block 0 of the update's
+// counter (c0, c1, t); later blocks only after a power-law trial rejects.
+__device__ __forceinline__ uint64_t draw_partner(const ZipfConsts& zc, const float* T, float B, uint64_t n,
+                                                 uint64_t i, bool cooling, uint32_t w2, uint32_t w3, uint32_t c0,
+                                                 uint32_t c1, uint32_t t, uint32_t key0, uint32_t key1) {
+    if (!cooling) {
+        const uint64_t x = mulhi64(((uint64_t)w3 << 32) | (w2 & ~15u), n - 1);
+        return x + (x >= i);
+    }
+    const uint64_t N = n - 1;
+    uint64_t k = 1;
+    bool ok = zipf_trial(zc, T, B, N, w3, k);
+    for (uint32_t blk = 1; !ok && blk < 17; ++blk) {  // trials 1..63
+        const uint4 x = philox4x32_10(make_uint4(c0, c1, t, blk), key0, key1);
+        ok = zipf_trial(zc, T, B, N, x.x, k) || zipf_trial(zc, T, B, N, x.y, k) ||
+             zipf_trial(zc, T, B, N, x.z, k) || (blk < 16 && zipf_trial(zc, T, B, N, x.w, k));
+    }
+    if (!ok) k = 1;
+    const bool fwd = (w2 >> 1) & 1u;
+    const bool can_fwd = i + k < n, can_bwd = i >= k;
+    if (fwd && can_fwd) return i + k;
+    if (!fwd && can_bwd) return i - k;
+    if (can_fwd) return i + k;
+    if (can_bwd) return i - k;
+    return (n - 1 - i > i) ? n - 1 : 0;
+}
+
 // Draw the pair of update u in iteration t (Algorithm 1, lines 5-11). One
 // Philox block serves the whole draw: w0, w1 pick the step, bits 0-3 of w2
 // are the coins, w3 feeds the first power-law trial or, with the upper 28
@@ -345,33 +373,9 @@ __device__ __forceinline__ Pair draw_pair(const SamplerArgs& a, const PathTable&
     r.w2 = w.z;
     r.cooling = (2ull * a.t >= a.T) || (w.z & 1u);
     r.short_path = n < 2;
-    if (r.short_path) { r.j = r.i; return r; }
-    uint64_t j;
-    if (r.cooling) {
-        const float B = pt.B[r.path];
-        const uint64_t N = n - 1;
-        uint64_t k = 1;
-        bool ok = zipf_trial(a.zc, pt.T, B, N, w.w, k);
-        for (uint32_t blk = 1; !ok && blk < 17; ++blk) {  // trials 1..63
-            const uint4 x = philox4x32_10(make_uint4(c0, c1, a.t, blk), a.key0, a.key1);
-            ok = zipf_trial(a.zc, pt.T, B, N, x.x, k) || zipf_trial(a.zc, pt.T, B, N, x.y, k) ||
-                 zipf_trial(a.zc, pt.T, B, N, x.z, k) ||
-                 (blk < 16 && zipf_trial(a.zc, pt.T, B, N, x.w, k));
-        }
-        if (!ok) k = 1;
-        const uint64_t i = r.i;
-        const bool fwd = (w.z >> 1) & 1u;
-        const bool can_fwd = i + k < n, can_bwd = i >= k;
-        if (fwd && can_fwd) j = i + k;
-        else if (!fwd && can_bwd) j = i - k;
-        else if (can_fwd) j = i + k;
-        else if (can_bwd) j = i - k;
-        else j = (n - 1 - i > i) ? n - 1 : 0;
-    } else {
-        const uint64_t x = mulhi64(((uint64_t)w.w << 32) | (w.z & ~15u), n - 1);
-        j = x + (x >= r.i);
-    }
-    r.j = j;
+    r.j = r.short_path ? r.i
+                       : draw_partner(a.zc, pt.T, pt.B[r.path], n, r.i, r.cooling, w.z, w.w, c0, c1, a.t, a.key0,
+                                      a.key1);
     return r;
 }
 
@@ -426,5 +430,79 @@ __device__ __forceinline__ Move pair_move(const NodeRec& a, int32_t axa, uint32_
     return m;
 }
 
+
+struct UpdateOpts {
+    float eta;
+    int store_mode;  // 0 = plain store, 1 = 64-bit atomic exchange
+    int pf64;        // 64-byte L2 prefetch hint: bit 0 step loads, bit 1 node loads
+    bool atomic;     // add the moves atomically instead of replacing the points
+};
+
+// UPT independent updates u0 + k * stride (k < UPT, only those below u_end)
+// of Algorithm 1, lines 5-15, kept in flight together: all draws first (ALU),
+// then all step-record loads, then all node-record loads, then the moves.
+template <int UPT>
+__device__ __forceinline__ void update_trip(const SamplerArgs& a, const PathTable& pt, NodeRec* __restrict__ nodes,
+                                            uint64_t u0, uint64_t stride, uint64_t u_end, const UpdateOpts& o,
+                                            uint64_t pol_stream, uint64_t pol_keep) {
+    const StepRec* __restrict__ steps = a.steps;
+    uint64_t gi[UPT], gj[UPT];
+    uint32_t w2[UPT];
+    bool act[UPT];
+#pragma unroll
+    for (int k = 0; k < UPT; ++k) {
+        const uint64_t u = u0 + (uint64_t)k * stride;
+        act[k] = u < u_end;
+        if (act[k]) {
+            const Pair pr = draw_pair(a, pt, u);
+            act[k] = !pr.short_path;
+            gi[k] = pr.base + pr.i;
+            gj[k] = pr.base + pr.j;
+            w2[k] = pr.w2;
+        }
+    }
+    StepRec si[UPT], sj[UPT];
+#pragma unroll
+    for (int k = 0; k < UPT; ++k) {
+        if (act[k]) {
+            si[k] = load_step(steps + gi[k], pol_stream, o.pf64 & 1);
+            sj[k] = load_step(steps + gj[k], pol_stream, o.pf64 & 1);
+        }
+    }
+    NodeRec na[UPT], nb[UPT];
+#pragma unroll
+    for (int k = 0; k < UPT; ++k) {
+        if (act[k]) {
+            na[k] = load_node(nodes + step_node(si[k]), pol_keep, o.pf64 & 2);
+            nb[k] = load_node(nodes + step_node(sj[k]), pol_keep, o.pf64 & 2);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < UPT; ++k) {
+        if (!act[k]) continue;
+        const uint32_t ea = (w2[k] >> 2) & 1u, eb = (w2[k] >> 3) & 1u;
+        const int64_t pa = endpoint_pos(si[k], ea), pb = endpoint_pos(sj[k], eb);
+        const int64_t d = pa > pb ? pa - pb : pb - pa;
+        if (d == 0) continue;
+        const Move m = pair_move(na[k], si[k].ax, ea, nb[k], sj[k].ax, eb, d, o.eta);
+        if (!m.moved) continue;
+        float* pa_ptr = &nodes[step_node(si[k])].sx + 2 * ea;
+        float* pb_ptr = &nodes[step_node(sj[k])].sx + 2 * eb;
+        if (o.atomic) {
+            atomicAdd(reinterpret_cast<float2*>(pa_ptr), make_float2(m.dxi, m.dyi));
+            atomicAdd(reinterpret_cast<float2*>(pb_ptr), make_float2(m.dxj, m.dyj));
+        } else {
+            const float xa = ea ? na[k].ex : na[k].sx, ya = ea ? na[k].ey : na[k].sy;
+            const float xb = eb ? nb[k].ex : nb[k].sx, yb = eb ? nb[k].ey : nb[k].sy;
+            if (o.store_mode == 0) {
+                *reinterpret_cast<float2*>(pa_ptr) = make_float2(xa + m.dxi, ya + m.dyi);
+                *reinterpret_cast<float2*>(pb_ptr) = make_float2(xb + m.dxj, yb + m.dyj);
+            } else {
+                exchange_point(pa_ptr, xa + m.dxi, ya + m.dyi, pol_keep);
+                exchange_point(pb_ptr, xb + m.dxj, yb + m.dyj, pol_keep);
+            }
+        }
+    }
+}
 
 }  // namespace pgsgd

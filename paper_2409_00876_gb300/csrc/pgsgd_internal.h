@@ -2,8 +2,13 @@
 // (pgsgd_kernels.cu). Not installed; no torch types anywhere.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
+#include <utility>
+#include <vector>
 #include <cuda_runtime.h>
+
+#include "../../include/pgsgd.h"
 
 #include "pgsgd_device.cuh"
 
@@ -20,7 +25,8 @@ enum : uint32_t {
     FLAG_COORD_NAN = 1u << 6,    // coordinate not finite
 };
 
-constexpr uint32_t kMaxPaths = 16384;
+constexpr uint32_t kMaxPaths = 16384;       // single graph: path tables in shared memory
+constexpr uint32_t kMaxBatchPaths = 1u << 22; // batch super graph: path tables in global memory
 
 struct UpdateLaunch {
     SamplerArgs s;
@@ -90,6 +96,76 @@ cudaError_t launch_pair_grad(const SamplerArgs& s, uint64_t u_begin, uint64_t co
 
 cudaError_t launch_full_stress(const StepRec* steps, const NodeRec* nodes, const uint64_t* path_off, uint32_t P,
                                uint64_t S, double* partials, int grid, cudaStream_t st);
+
+}  // namespace pgsgd
+
+// The state behind a pgsgd_graph handle (device arrays are owned).
+struct pgsgd_graph {
+    using NodeRec = pgsgd::NodeRec;
+    using StepRec = pgsgd::StepRec;
+    int device = 0;
+    int sm_count = 0;
+    uint32_t n_nodes = 0, n_paths = 0;
+    uint64_t n_steps = 0;
+    uint64_t max_path_steps = 0;
+    int64_t max_path_nt = 0;
+    std::vector<uint64_t> h_path_off;
+    std::vector<int64_t> h_path_nt;    // nucleotide length of every path
+
+    NodeRec* d_nodes = nullptr;
+    int32_t* d_anchor = nullptr;       // [V] x anchors (master copy)
+    StepRec* d_steps = nullptr;
+    uint64_t* d_path_off = nullptr;
+    uint64_t* d_sample_off = nullptr;  // stress sample offsets [P + 1]
+    float* d_zipf_B = nullptr;
+    float* d_zipf_T = nullptr;         // [kZipfTable] acceptance thresholds
+    uint16_t* d_guide = nullptr;       // [n_guide + 1]
+    uint32_t n_guide = 1, guide_shift = 0;
+    uint32_t* d_flags = nullptr;
+    uint32_t* d_changed = nullptr;     // set by a rebase that moved an anchor
+    double* d_partials = nullptr;      // stress scratch [max_stress_blocks][3] + 3 totals
+    double* d_per_path = nullptr;      // [P][3]
+    double* d_xy = nullptr;            // coordinate staging [V][4]
+    void* d_debug = nullptr;           // debug output staging
+    size_t debug_bytes = 0;
+    int max_stress_blocks = 0;
+    uint64_t stress_samples_per_step = 0;
+
+    bool has_coords = false;
+    float zipf_theta = NAN;
+
+    // options
+    int coord_mode = 0;
+    int updates_per_step = 10;
+    int block = 256;
+    int blocks_per_sm = 32;
+    int upt = 2;
+    int atomic = 0;
+    int rebase = 1;
+    int timing = 0;
+    int64_t max_concurrent = -1;  // -1 = automatic
+    int min_blocks = 1;
+    int l2_fetch = 0;
+    int store_mode = 1;  // 64-bit atomic exchange: measured fastest replace-store
+    int l2_hints = 1;
+    int pf64 = 3;
+
+    // timing
+    std::vector<cudaEvent_t> ev_free;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+    double timing_ms = 0.0;
+    uint64_t timing_launches = 0, timing_updates = 0;
+
+    uint64_t device_bytes = 0;
+};
+
+namespace pgsgd {
+
+int graph_create(const uint32_t* node_len, uint32_t n_nodes, const uint64_t* path_off, uint32_t n_paths,
+                 const uint32_t* step_node, const uint8_t* step_rev, const int64_t* step_pos, int on_device,
+                 void* cuda_stream, bool batch, pgsgd_graph** out);
+void free_graph(pgsgd_graph* g);
+int ensure_zipf(pgsgd_graph* g, float theta, cudaStream_t st);
 
 // Record the calling thread's error message (read by pgsgd_last_error) and
 // return status.

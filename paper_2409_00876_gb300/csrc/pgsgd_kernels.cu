@@ -16,6 +16,8 @@ namespace pgsgd {
 
 namespace {
 
+constexpr uint32_t kPackStagedPaths = 16384;  // 128 KiB of path offsets in shared memory
+
 // ---------------------------------------------------------------- ingest
 
 __global__ void check_lengths_kernel(const uint32_t* __restrict__ node_len, uint32_t n, uint32_t* flags) {
@@ -32,15 +34,19 @@ __global__ void pack_steps_kernel(const uint32_t* __restrict__ step_node,
                                   const uint32_t* __restrict__ node_len, uint32_t n_nodes,
                                   const uint64_t* __restrict__ path_off, uint32_t P, uint64_t S,
                                   StepRec* __restrict__ steps, uint32_t* flags) {
+    // path offsets staged in shared memory unless there are too many paths
     extern __shared__ uint64_t s_off[];
-    for (uint32_t k = threadIdx.x; k <= P; k += blockDim.x) s_off[k] = path_off[k];
+    const bool staged = P <= kPackStagedPaths;
+    if (staged)
+        for (uint32_t k = threadIdx.x; k <= P; k += blockDim.x) s_off[k] = path_off[k];
     __syncthreads();
+    const uint64_t* off = staged ? s_off : path_off;
     uint32_t bad = 0;
     for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < S;
          s += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t p = find_path(s_off, P, s);
-        const bool first = s == s_off[p];
-        const bool last = s + 1 == s_off[p + 1];
+        const uint32_t p = find_path(off, P, s);
+        const bool first = s == off[p];
+        const bool last = s + 1 == off[p + 1];
         const uint32_t nd = step_node[s];
         const uint32_t rv = step_rev[s];
         const int64_t ps = step_pos[s];
@@ -172,9 +178,7 @@ __global__ void zipf_setup_kernel(const uint64_t* __restrict__ path_off, uint32_
 // ---------------------------------------------------------------- the update kernel
 
 // One launch = one iteration's N updates (or a slice), grid-stride over the
-// update index u. Every thread keeps UPT independent updates in flight per
-// loop trip: all draws first (ALU), then all step-record loads, then all
-// node-record loads, then the moves.
+// update index u; every loop trip is one update_trip of UPT updates.
 template <int UPT, int MINB>
 __global__ void __launch_bounds__(256, MINB) update_kernel(UpdateLaunch L) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -186,67 +190,10 @@ __global__ void __launch_bounds__(256, MINB) update_kernel(UpdateLaunch L) {
     const uint64_t pol_keep = L.l2_hints ? policy_evict_last() : 0;
     const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t gtid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    const StepRec* __restrict__ steps = a.steps;
-    NodeRec* __restrict__ nodes = L.nodes;
-    for (uint64_t base = gtid; base < L.n_updates; base += nthr * UPT) {
-        uint64_t gi[UPT], gj[UPT];
-        uint32_t w2[UPT];
-        bool act[UPT];
-#pragma unroll
-        for (int k = 0; k < UPT; ++k) {
-            const uint64_t u = base + (uint64_t)k * nthr;
-            act[k] = u < L.n_updates;
-            if (act[k]) {
-                const Pair pr = draw_pair(a, pt, L.u_begin + u);
-                act[k] = !pr.short_path;
-                gi[k] = pr.base + pr.i;
-                gj[k] = pr.base + pr.j;
-                w2[k] = pr.w2;
-            }
-        }
-        StepRec si[UPT], sj[UPT];
-#pragma unroll
-        for (int k = 0; k < UPT; ++k) {
-            if (act[k]) {
-                si[k] = load_step(steps + gi[k], pol_stream, L.pf64 & 1);
-                sj[k] = load_step(steps + gj[k], pol_stream, L.pf64 & 1);
-            }
-        }
-        NodeRec na[UPT], nb[UPT];
-#pragma unroll
-        for (int k = 0; k < UPT; ++k) {
-            if (act[k]) {
-                na[k] = load_node(nodes + step_node(si[k]), pol_keep, L.pf64 & 2);
-                nb[k] = load_node(nodes + step_node(sj[k]), pol_keep, L.pf64 & 2);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < UPT; ++k) {
-            if (!act[k]) continue;
-            const uint32_t ea = (w2[k] >> 2) & 1u, eb = (w2[k] >> 3) & 1u;
-            const int64_t pa = endpoint_pos(si[k], ea), pb = endpoint_pos(sj[k], eb);
-            const int64_t d = pa > pb ? pa - pb : pb - pa;
-            if (d == 0) continue;
-            const Move m = pair_move(na[k], si[k].ax, ea, nb[k], sj[k].ax, eb, d, L.eta);
-            if (!m.moved) continue;
-            float* pa_ptr = &nodes[step_node(si[k])].sx + 2 * ea;
-            float* pb_ptr = &nodes[step_node(sj[k])].sx + 2 * eb;
-            if (L.atomic) {
-                atomicAdd(reinterpret_cast<float2*>(pa_ptr), make_float2(m.dxi, m.dyi));
-                atomicAdd(reinterpret_cast<float2*>(pb_ptr), make_float2(m.dxj, m.dyj));
-            } else {
-                const float xa = ea ? na[k].ex : na[k].sx, ya = ea ? na[k].ey : na[k].sy;
-                const float xb = eb ? nb[k].ex : nb[k].sx, yb = eb ? nb[k].ey : nb[k].sy;
-                if (L.store_mode == 0) {
-                    *reinterpret_cast<float2*>(pa_ptr) = make_float2(xa + m.dxi, ya + m.dyi);
-                    *reinterpret_cast<float2*>(pb_ptr) = make_float2(xb + m.dxj, yb + m.dyj);
-                } else {
-                    exchange_point(pa_ptr, xa + m.dxi, ya + m.dyi, pol_keep);
-                    exchange_point(pb_ptr, xb + m.dxj, yb + m.dyj, pol_keep);
-                }
-            }
-        }
-    }
+    const UpdateOpts o{L.eta, L.store_mode, L.pf64, L.atomic};
+    const uint64_t u_end = L.u_begin + L.n_updates;
+    for (uint64_t base = L.u_begin + gtid; base < u_end; base += nthr * UPT)
+        update_trip<UPT>(a, pt, L.nodes, base, nthr, u_end, o, pol_stream, pol_keep);
 }
 
 // ---------------------------------------------------------------- debug kernels
@@ -464,7 +411,7 @@ cudaError_t launch_pack_steps(const uint32_t* step_node, const uint8_t* step_rev
                               uint32_t n_paths, uint64_t n_steps, StepRec* steps, uint32_t* flags,
                               int sm_count, cudaStream_t st) {
     if (n_steps == 0) return cudaSuccess;
-    const size_t smem = (size_t)(n_paths + 1) * sizeof(uint64_t);
+    const size_t smem = n_paths <= kPackStagedPaths ? (size_t)(n_paths + 1) * sizeof(uint64_t) : 0;
     cudaError_t e = cudaFuncSetAttribute(pack_steps_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;

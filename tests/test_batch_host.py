@@ -1,0 +1,83 @@
+"""Host-side logic of the batched layout (no GPU): the batch generator, its
+concatenation, and the schedule plan the library computes on the host."""
+import numpy as np
+import pytest
+
+from synth import batch_shapes, concat, make_batch, make_graph
+
+
+def test_batch_shapes_follow_the_workload_ranges():
+    sh = batch_shapes(256, (1_000, 200_000), (4, 90), 11)
+    v = np.array([a for a, _, _ in sh])
+    p = np.array([b for _, b, _ in sh])
+    assert len(sh) == 256
+    assert v.min() >= 1_000 and v.max() <= 200_000
+    assert p.min() >= 4 and p.max() <= 90
+    # log-uniform: about half the graphs below the geometric midpoint
+    mid = np.sqrt(1_000 * 200_000)
+    assert 0.4 < np.mean(v < mid) < 0.6
+    assert len({s for _, _, s in sh}) == 256
+
+
+def test_concat_keeps_every_graph_intact():
+    gs = make_batch("batch_small")
+    b = concat(gs)
+    assert b.n_graphs == len(gs)
+    for k, g in enumerate(gs):
+        n0, n1 = int(b.graph_node_off[k]), int(b.graph_node_off[k + 1])
+        p0, p1 = int(b.graph_path_off[k]), int(b.graph_path_off[k + 1])
+        assert n1 - n0 == g.n_nodes and p1 - p0 == g.n_paths
+        s0, s1 = int(b.path_off[p0]), int(b.path_off[p1])
+        np.testing.assert_array_equal(b.path_off[p0:p1 + 1] - b.path_off[p0], g.path_off)
+        np.testing.assert_array_equal(b.step_node[s0:s1], g.step_node)
+        np.testing.assert_array_equal(b.step_pos[s0:s1], g.step_pos)
+        np.testing.assert_array_equal(b.node_len[n0:n1], g.node_len)
+        np.testing.assert_array_equal(b.graph_xy(b.init_xy, k), g.init_xy)
+    # node counts near the requested ones (backbone plus about 10 % bubble nodes)
+    want = [v for v, _, _ in batch_shapes(12, (1_000, 12_000), (4, 12), 5)]
+    got = [g.n_nodes for g in gs]
+    assert np.all(np.abs(np.array(got) / np.array(want) - 1) < 0.05)
+
+
+def _plan(*a, **k):
+    from paper_2409_00876_gb300.batch import plan
+    return plan(*a, **k)
+
+
+def test_plan_orders_by_work_and_caps_lanes():
+    nu = np.array([100, 0, 5000, 5000, 70000], np.uint64)
+    nn = np.array([10, 5, 4000, 100000, 3000], np.uint64)
+    r2g, nch, lanes = _plan(nu, nn, block=256, updates_per_thread=2, chunk=1000)
+    # most updates first, ties by graph index
+    assert list(r2g) == [4, 2, 3, 0, 1]
+    np.testing.assert_array_equal(nch, [1, 0, 5, 5, 70])
+    # cap = max(2048, V / 2) updates in flight = cap // 512 chunks, at most the chunks there are
+    caps = np.maximum(2048, nn // 2) // 512
+    np.testing.assert_array_equal(lanes, np.where(nch == 0, 0, np.minimum(np.maximum(caps, 1), nch)))
+
+
+def test_plan_options_change_lanes():
+    nu = np.array([10_000_000], np.uint64)
+    nn = np.array([200_000], np.uint64)
+    _, nch, lanes = _plan(nu, nn, block=128, updates_per_thread=4, chunk=4096)
+    assert nch[0] == -(-10_000_000 // 4096)
+    assert lanes[0] == 100_000 // 512
+    _, _, lanes0 = _plan(nu, nn, chunk=4096, max_concurrent=0)
+    assert lanes0[0] == nch[0]  # no cap: every chunk may run at once
+    _, _, lanes1 = _plan(nu, nn, chunk=4096, max_concurrent=100)
+    assert lanes1[0] == 1
+
+
+@pytest.mark.parametrize("kw", [dict(block=48), dict(block=288), dict(updates_per_thread=3), dict(chunk=0),
+                                dict(max_concurrent=-2)])
+def test_plan_rejects_bad_options(kw):
+    from paper_2409_00876_gb300 import PgsgdError
+    with pytest.raises(PgsgdError):
+        _plan([10], [10], **kw)
+
+
+def test_batch_of_one_graph_matches_its_arrays():
+    g = make_graph("tiny")
+    b = concat([g])
+    np.testing.assert_array_equal(b.path_off, g.path_off)
+    assert list(b.graph_node_off) == [0, g.n_nodes]
