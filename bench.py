@@ -48,7 +48,12 @@ WORKLOADS = {
     "tiny": "synthetic pangenome: 2,000 backbone nodes, 8 paths, ~1.6e4 steps",
     "prof": "synthetic chromosome-like pangenome for profiling: 2,000,000 backbone nodes, "
             "30 paths, ~6.3e7 steps (0.6 GB on device, above L2)",
+    "batch256": "256 independent synthetic subgraphs, node counts log-uniform in [1,000, 200,000], "
+                "path counts uniform in [4, 90] (8.6e6 nodes, 4.0e8 steps in all); 30 iterations "
+                "x 10 x steps updates per graph, each graph with its own learning-rate schedule",
 }
+BATCH_METRIC = "PG-SGD updates/sec, batched layout of 256 subgraphs (one persistent or CUDA-graph launch " \
+               "sequence) vs one launch per graph; per-graph stress"
 
 
 # ---------------------------------------------------------------- distributed
@@ -161,7 +166,13 @@ class ClockSampler:
 # ---------------------------------------------------------------- workload
 
 def make_workload(config):
-    from synth import make_graph
+    from synth import BATCH_CONFIGS, batch_shapes, make_batch, make_graph
+    if config == "batch256":
+        # the oracle's bounded sample runs on the batch's largest graph
+        cfg = BATCH_CONFIGS["batch256"]
+        shapes = batch_shapes(cfg["n_graphs"], cfg["nodes"], cfg["paths"], cfg["seed"])
+        k = max(range(len(shapes)), key=lambda i: shapes[i][0] * shapes[i][1])
+        return make_batch("batch256", indices=[k])[0]
     if config == "prof":
         return make_graph("chrom", backbone=2_000_000, paths=30)
     return make_graph(config)
@@ -302,6 +313,10 @@ def run_gpu(args):
     if rank == 0 and ws == 1 and not args.skip_cpu:
         cpu = cpu_baseline(g, budget_s=args.cpu_budget)
 
+    forms = None
+    if rank == 0 and not args.no_forms and args.config == "chrom":
+        forms = {"batched": batch_form(dev), "differentiable": dstress_form(dev)}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -324,6 +339,201 @@ def run_gpu(args):
             "gpu_launches": gpu_launches,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "forms": forms,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- batched and differentiable forms
+
+def _batch_timed(B, xy, seeds, iter_end=None):
+    """Milliseconds of one full layout from xy (library events on the stream)."""
+    B.set_coords(xy)
+    B.set_option("timing", 1)
+    B.timing_read(reset=True)
+    B.layout(ITERS, seeds=seeds, theta=THETA, iter_end=iter_end)
+    ms, launches, updates = B.timing_read(reset=True)
+    B.set_option("timing", 0)
+    return ms, launches, updates
+
+
+def batch_form(dev, full=False, log=None):
+    """The 256-subgraph batch: autotuned batched schedule against one launch
+    per graph (and, with full, the other schedules and separate one-graph
+    handles), every schedule from the same initial layouts and seeds."""
+    import torch
+    import paper_2409_00876_gb300 as pg
+    from paper_2409_00876_gb300.batch import Batch, autotune
+    from synth import concat, make_batch
+    gs = make_batch("batch256")
+    arr = concat(gs)
+    B = Batch.from_arrays(arr)
+    xy = torch.from_numpy(arr.init_xy).to(dev)
+    seeds = np.arange(1, len(gs) + 1, dtype=np.uint64)
+    updates = ITERS * 10 * sum(g.n_steps for g in gs)
+    t0 = time.perf_counter()
+    tuned, table = autotune(B, xy, seeds=seeds, iter_max=ITERS, theta=THETA, log=log)
+    tune_s = time.perf_counter() - t0
+
+    def stress_summary():
+        st = B.stress(STRESS_PER_STEP, seed=STRESS_SEED)
+        m = np.array([r["mean"] for r in st])
+        return {"mean_over_graphs": float(m.mean()), "median": float(np.median(m)), "max": float(m.max())}
+
+    _batch_timed(B, xy, seeds)  # warm: the tuned shape's CUDA graph
+    ms, launches, _ = _batch_timed(B, xy, seeds)
+    out = {"workload": WORKLOADS["batch256"], "n_graphs": len(gs), "updates": updates,
+           "tuned": {**tuned, "mode": {0: "launch per iteration (CUDA graph)", 1: "persistent", 2: "per graph"}[
+               tuned["mode"]]}, "autotune_s": round(tune_s, 1),
+           "autotune_trials_ms": {"/".join(map(str, k)): round(v, 2) for k, v in table.items()},
+           "autotune_keys": "mode/updates_per_thread/block/chunk",
+           "batched": {"ms": ms, "updates_per_s": updates / (ms / 1e3), "launches": launches,
+                       "stress": stress_summary()}}
+    others = [("per_graph_launches", dict(mode=2, cuda_graph=0))]
+    if full:
+        others = [("launch_per_iteration", dict(mode=0, cuda_graph=1)), ("persistent", dict(mode=1)),
+                  ("per_graph_launches_cuda_graph", dict(mode=2, cuda_graph=1))] + others
+    for name, opts in others:
+        for k, v in opts.items():
+            B.set_option(k, v)
+        _batch_timed(B, xy, seeds, iter_end=1)
+        ms2, launches2, _ = _batch_timed(B, xy, seeds)
+        out[name] = {"ms": ms2, "updates_per_s": updates / (ms2 / 1e3), "launches": launches2,
+                     "stress": stress_summary()}
+    out["speedup_vs_per_graph_launches"] = out["per_graph_launches"]["ms"] / out["batched"]["ms"]
+    if full:
+        Gs = [pg.Graph.from_synth(g) for g in gs]
+        for G, g in zip(Gs, gs):
+            G.set_coords(g.init_xy)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k, G in enumerate(Gs):
+            G.layout(ITERS, theta=THETA, seed=int(seeds[k]))
+        e1.record()
+        torch.cuda.synchronize()
+        ms3 = e0.elapsed_time(e1)
+        m = np.array([G.stress(STRESS_PER_STEP, seed=STRESS_SEED)["mean"] for G in Gs])
+        out["one_graph_handles"] = {"ms": ms3, "updates_per_s": updates / (ms3 / 1e3),
+                                    "stress": {"mean_over_graphs": float(m.mean()),
+                                               "median": float(np.median(m)), "max": float(m.max())}}
+    B.close()
+    return out
+
+
+def dstress_form(dev, n_pairs=10_000_000, steps=200):
+    """Differentiable sampled stress on the laid-out 200 k-node graph: forward
+    and backward kernel times for 10 M pairs, and a 200-step full-batch
+    refinement from the PG-SGD result (Adam on the hand-written gradient)."""
+    import torch
+    import paper_2409_00876_gb300 as pg
+    from paper_2409_00876_gb300.autograd import refine
+    from synth import make_graph
+    g = make_graph("mid")
+    G = pg.Graph.from_synth(g)
+    G.set_coords(g.init_xy)
+    G.layout(ITERS, theta=THETA, seed=SEED)
+    xy = torch.empty((g.n_nodes, 4), dtype=torch.float64, device=dev)
+    G.get_coords(xy)
+    grad = torch.empty((g.n_nodes, 4), dtype=torch.float32, device=dev)
+    fw, bw = [], []
+    for i in range(4):
+        t0 = time.perf_counter()
+        _, n_valid = G.dstress(n_pairs, 3)
+        t1 = time.perf_counter()
+        G.dstress_backward(n_pairs, 3, 1.0 / n_valid, grad)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        if i:
+            fw.append(t1 - t0)
+            bw.append(t2 - t1)
+    before = G.stress(STRESS_PER_STEP, seed=STRESS_SEED)["mean"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    xr, trace = refine(G, xy, steps=steps, lr=0.05, n_pairs=n_pairs, seed=9)
+    torch.cuda.synchronize()
+    ref_s = time.perf_counter() - t0
+    G.set_coords(xr)
+    after = G.stress(STRESS_PER_STEP, seed=STRESS_SEED)["mean"]
+    return {"workload": WORKLOADS["mid"] + ", after a 30-iteration PG-SGD layout", "pairs": n_pairs,
+            "forward_ms": 1e3 * min(fw), "backward_ms": 1e3 * min(bw),
+            "pairs_per_s_backward": n_pairs / min(bw),
+            "refine_steps": steps, "refine_s": ref_s, "objective_first": trace[0], "objective_last": trace[-1],
+            "stress_before": before, "stress_after": after, "stress_change": after - before,
+            "timing": "host wall clock around synchronous calls (forward includes its readback)"}
+
+
+def run_batch(args):
+    """--config batch256: one JSON line for the batched schedule."""
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    init_dist("nccl" if ws > 1 else "gloo")
+    dev = torch.device("cuda", local)
+    import paper_2409_00876_gb300 as pg
+    from paper_2409_00876_gb300.batch import Batch, autotune
+    from synth import concat, make_batch
+    pg.load_library()
+    gs = make_batch("batch256")
+    arr = concat(gs)
+    B = Batch.from_arrays(arr)
+    xy = torch.from_numpy(arr.init_xy).to(dev)
+    seeds = np.arange(1, len(gs) + 1, dtype=np.uint64)
+    tuned, _ = autotune(B, xy, seeds=seeds, iter_max=ITERS, theta=THETA)
+    S = sum(g.n_steps for g in gs)
+    updates_per_step = ITERS * 10 * S
+    stream = torch.cuda.current_stream()
+
+    def step():
+        B.set_coords(xy)
+        B.layout(ITERS, seeds=seeds, theta=THETA)
+        return B.stress(STRESS_PER_STEP, seed=STRESS_SEED)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    B.set_option("timing", 1)
+    B.timing_read(reset=True)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        st = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    lay_ms, launches, upd = B.timing_read(reset=True)
+    B.set_option("timing", 0)
+    ms_max = max_over_ranks(ms, dev)
+    value = sum_over_ranks(updates_per_step * args.steps, dev) / (ms_max / 1e3)
+    peak, peak_kind = peaks()
+    achieved = BYTES_PER_UPDATE * upd / (lay_ms / 1e3) / 1e9
+    B.close()
+    comp = batch_form(dev, full=True) if rank == 0 else None
+    if rank == 0:
+        m = np.array([r["mean"] for r in st])
+        per_launch = {0: ITERS, 1: 1, 2: ITERS * len(gs)}[tuned["mode"]]
+        line = {
+            "metric": BATCH_METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOADS["batch256"], "name": "batch256", "n_steps": S,
+                       "updates_per_step": updates_per_step, "tuned": tuned,
+                       "l2": "inputs larger than L2 (6.6 GB of step records), no flush",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "stress": {"mean_over_graphs": float(m.mean()), "max": float(m.max())},
+            "layout_only_updates_per_s": upd / (lay_ms / 1e3),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "batch layout kernels",
+                         "bytes_per_update_model": BYTES_PER_UPDATE, "peak_kind": peak_kind},
+            "clocks": clk,
+            "gpu_launches": args.steps * (2 + per_launch + 1),
+            "comparison": comp,
         }
         print(json.dumps(line), flush=True)
     return 0
@@ -402,11 +612,15 @@ def main(argv=None):
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-budget", type=float, default=10.0)
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the batched and differentiable forms on the chromosome run")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "gb300" and not os.environ.get("PGSGD_BENCH_ALLOW_SHORT"):
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.config == "batch256":
+        return run_batch(args)
     return run_gpu(args)
 
 

@@ -31,12 +31,15 @@ def batch_shapes(n_graphs, nodes, paths, seed):
     return [(int(a), int(b), int(c)) for a, b, c in zip(v, p, gs)]
 
 
-def make_batch(name_or_cfg="batch256", **overrides) -> list[Graph]:
+def make_batch(name_or_cfg="batch256", indices=None, **overrides) -> list[Graph]:
+    """The batch's graphs (only those at `indices`, if given)."""
     cfg = dict(BATCH_CONFIGS[name_or_cfg]) if isinstance(name_or_cfg, str) else dict(name_or_cfg)
     cfg.update(overrides)
     base = dict(CONFIGS[cfg["base"]])
+    shapes = batch_shapes(cfg["n_graphs"], cfg["nodes"], cfg["paths"], cfg["seed"])
     graphs = []
-    for v, p, gs in batch_shapes(cfg["n_graphs"], cfg["nodes"], cfg["paths"], cfg["seed"]):
+    for k in (range(len(shapes)) if indices is None else indices):
+        v, p, gs = shapes[k]
         backbone = max(2, int(round(v / (1.0 + base["p_site"]))))
         graphs.append(make_graph(base, gen_seed=gs, backbone=backbone, paths=p))
     return graphs
