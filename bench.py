@@ -101,6 +101,11 @@ def sum_over_ranks(x: float, device=None) -> float:
     return float(t.item())
 
 
+def aggregate_rate(units: float, ms: float, device=None) -> float:
+    """Whole-job rate: the units all ranks processed / the slowest rank's time."""
+    return sum_over_ranks(units, device) / (max_over_ranks(ms, device) / 1e3)
+
+
 # ---------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -287,8 +292,7 @@ def run_gpu(args):
     upd_ms, launches, upd = G.timing_read(reset=True)
     G.set_option("timing", 0)
     ms_max = max_over_ranks(ms, dev)
-    total_updates = sum_over_ranks(updates_per_step * args.steps, dev)
-    value = total_updates / (ms_max / 1e3)
+    value = aggregate_rate(updates_per_step * args.steps, ms, dev)
 
     # kernels launched per step: set_coords + anchor refresh, 30 x (update +
     # rebase + anchor refresh), stress + finalize
@@ -307,7 +311,7 @@ def run_gpu(args):
     # end to end through the public API with host buffers, copies inside the region
     e2e = run_e2e(pg, g, args, dev) if not args.skip_e2e else None
     if e2e is not None:
-        e2e["value"] = sum_over_ranks(e2e.pop("updates"), dev) / max_over_ranks(e2e.pop("seconds"), dev)
+        e2e["value"] = aggregate_rate(e2e.pop("updates"), 1e3 * e2e.pop("seconds"), dev)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.skip_cpu:
@@ -387,7 +391,7 @@ def batch_form(dev, full=False, log=None):
            "tuned": {**tuned, "mode": {0: "launch per iteration (CUDA graph)", 1: "persistent", 2: "per graph"}[
                tuned["mode"]]}, "autotune_s": round(tune_s, 1),
            "autotune_trials_ms": {"/".join(map(str, k)): round(v, 2) for k, v in table.items()},
-           "autotune_keys": "mode/updates_per_thread/block/chunk",
+           "autotune_keys": "mode/pipeline/updates_per_thread/block/chunk",
            "batched": {"ms": ms, "updates_per_s": updates / (ms / 1e3), "launches": launches,
                        "stress": stress_summary()}}
     others = [("per_graph_launches", dict(mode=2, cuda_graph=0))]
@@ -510,7 +514,7 @@ def run_batch(args):
     lay_ms, launches, upd = B.timing_read(reset=True)
     B.set_option("timing", 0)
     ms_max = max_over_ranks(ms, dev)
-    value = sum_over_ranks(updates_per_step * args.steps, dev) / (ms_max / 1e3)
+    value = aggregate_rate(updates_per_step * args.steps, ms, dev)
     peak, peak_kind = peaks()
     achieved = BYTES_PER_UPDATE * upd / (lay_ms / 1e3) / 1e9
     B.close()

@@ -97,11 +97,19 @@ typedef enum pgsgd_option {
      * node records read and written evict-last, so the node array stays in
      * L2 while the step records stream past. 0 = no hints. */
     PGSGD_OPT_L2_HINTS = 13,
-    /* 64-byte L2 prefetch-size hint on the update kernel's record loads:
-     * bit 0 = step records, bit 1 = node records. Default 3 (both): without
-     * it a random 32-byte miss was promoted to 128 bytes, and the full
-     * chromosome layout ran at 14.4e9 instead of 18.6e9 updates/s. */
-    PGSGD_OPT_PREFETCH64 = 14
+    /* 64-byte L2 prefetch-size hint on record loads: bit 0 = step records,
+     * bit 1 = node records of the update kernel; bits 2 and 3 the same for
+     * the sampled-stress kernel. Default 7 (both update-kernel loads, the
+     * stress kernel's step loads): without it a random 32-byte miss of the
+     * update kernel was promoted to 128 bytes, and the full chromosome
+     * layout ran at 14.4e9 instead of 18.6e9 updates/s; the stress kernel's
+     * step hint gained 3 % and its node hint lost 8 %. */
+    PGSGD_OPT_PREFETCH64 = 14,
+    /* 1 = software-pipelined update loop: each thread issues a trip's
+     * step-record loads, then draws the next trip's pairs while they are in
+     * flight (same draws and moves; compiled for updates per thread / min
+     * blocks 1/1, 1/3, 2/1, 2/2 and 4/1). Default 0. */
+    PGSGD_OPT_PIPELINE = 15
 } pgsgd_option;
 
 /* Device-resident graph: node records, packed step records, path table. */

@@ -70,7 +70,13 @@ typedef enum pgsgd_batch_option {
     PGSGD_BOPT_STALL_TEST = 10,
     /* Mode 1: resident blocks per SM in the persistent grid; 0 (default) =
      * as many as the occupancy calculator allows. */
-    PGSGD_BOPT_BLOCKS_PER_SM = 11
+    PGSGD_BOPT_BLOCKS_PER_SM = 11,
+    /* 1 = the software-pipelined update loop (PGSGD_OPT_PIPELINE of
+     * pgsgd.h) inside every chunk. Default 0. */
+    PGSGD_BOPT_PIPELINE = 12,
+    /* 64-byte L2 prefetch-size hints, bits as PGSGD_OPT_PREFETCH64 of
+     * pgsgd.h (bits 0-1 update kernels, bits 2-3 stress kernel). Default 7. */
+    PGSGD_BOPT_PREFETCH64 = 13
 } pgsgd_batch_option;
 
 typedef struct pgsgd_batch_info {

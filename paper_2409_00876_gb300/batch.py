@@ -1,8 +1,8 @@
 """Batched layout of many independent graphs (include/pgsgd_batch.h).
 
 Argument marshalling over libpgsgd.so, plus ``autotune``, which picks the
-batch schedule (mode, threads per block, updates per thread, chunk size) by
-timing short layouts on the GPU. Every step of the layout runs in the
+batch schedule (mode, pipelined loop, threads per block, updates per thread,
+chunk size) by timing short layouts on the GPU. Every step of the layout runs in the
 library's CUDA kernels.
 """
 from __future__ import annotations
@@ -191,7 +191,7 @@ def autotune(b, xy, seeds=1, iter_max=30, theta=0.99, window=None, repeats=1, sp
     b and returns (best options, {options tuple: ms})."""
     if window is None:
         window = (iter_max // 2 - 1, iter_max // 2 + 1)
-    space = space or dict(mode=[0, 1], updates_per_thread=[2, 1, 4], block=[256, 128],
+    space = space or dict(mode=[0, 1], pipeline=[0, 1], updates_per_thread=[2, 1, 4], block=[256, 128],
                           chunk=[16384, 4096, 65536])
     keys = list(space)
     cur = {k: b.get_option(k) for k in keys}

@@ -419,8 +419,11 @@ int pgsgd_set_option(pgsgd_graph* g, int option, int64_t v) {
             g->l2_hints = v ? 1 : 0;
             return PGSGD_OK;
         case PGSGD_OPT_PREFETCH64:
-            if (v < 0 || v > 3) return fail(PGSGD_EINVAL, "prefetch option must be in [0, 3]");
+            if (v < 0 || v > 15) return fail(PGSGD_EINVAL, "prefetch option must be in [0, 15]");
             g->pf64 = (int)v;
+            return PGSGD_OK;
+        case PGSGD_OPT_PIPELINE:
+            g->pipeline = v ? 1 : 0;
             return PGSGD_OK;
         case PGSGD_OPT_L2_FETCH:
             if (v != 0 && v != 32 && v != 64 && v != 128)
@@ -449,6 +452,7 @@ int pgsgd_get_option(const pgsgd_graph* g, int option, int64_t* v) {
         case PGSGD_OPT_STORE_MODE: *v = g->store_mode; return PGSGD_OK;
         case PGSGD_OPT_L2_HINTS: *v = g->l2_hints; return PGSGD_OK;
         case PGSGD_OPT_PREFETCH64: *v = g->pf64; return PGSGD_OK;
+        case PGSGD_OPT_PIPELINE: *v = g->pipeline; return PGSGD_OK;
         default: return fail(PGSGD_EINVAL, "unknown option %d", option);
     }
 }
@@ -557,6 +561,7 @@ int pgsgd_layout(pgsgd_graph* g, uint32_t iter_max, const double* eta, double et
     L.store_mode = g->store_mode;
     L.l2_hints = g->l2_hints != 0;
     L.pf64 = g->pf64;
+    L.pipeline = g->pipeline != 0;
     L.atomic = g->atomic != 0;
     if (g->l2_fetch) CK(cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, g->l2_fetch), "L2 fetch limit");
     for (uint32_t t = iter_begin; t < iter_end; ++t) {
@@ -640,6 +645,7 @@ int pgsgd_stress(pgsgd_graph* g, uint32_t samples_per_step, uint64_t seed, pgsgd
     L.key1 = (uint32_t)(seed >> 32);
     L.partials = g->d_partials;
     L.per_path = per_path ? g->d_per_path : nullptr;
+    L.pf64 = (g->pf64 >> 2) & 3;
     L.block = 256;
     const uint64_t want = (n_samples + 2 * 256 - 1) / (2 * 256);
     L.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)g->max_stress_blocks));

@@ -172,7 +172,7 @@ __device__ __forceinline__ SamplerArgs graph_sampler(const BatchLaunch& L, const
 
 // The updates [c * chunk, min((c + 1) * chunk, N_g)) of iteration t of the
 // graph of rank r, by the whole block.
-template <int UPT>
+template <int UPT, bool PIPE>
 __device__ __forceinline__ void run_chunk(const BatchLaunch& L, const BatchGraph& G, uint32_t r, const BatchSmem& s,
                                           const ZipfConsts& zc, uint32_t t, uint32_t c, uint64_t pol_stream,
                                           uint64_t pol_keep) {
@@ -181,14 +181,18 @@ __device__ __forceinline__ void run_chunk(const BatchLaunch& L, const BatchGraph
     const UpdateOpts o{L.eta[(uint64_t)r * L.T + t], L.store_mode, L.pf64, false};
     const uint64_t cb = (uint64_t)c * L.chunk;
     const uint64_t ce = min(cb + L.chunk, G.n_updates);
-    for (uint64_t base = cb + threadIdx.x; base < ce; base += (uint64_t)blockDim.x * UPT)
-        update_trip<UPT>(a, pt, L.nodes, base, blockDim.x, ce, o, pol_stream, pol_keep);
+    if (PIPE) {
+        update_range_pipelined<UPT>(a, pt, L.nodes, cb + threadIdx.x, blockDim.x, ce, o, pol_stream, pol_keep);
+    } else {
+        for (uint64_t base = cb + threadIdx.x; base < ce; base += (uint64_t)blockDim.x * UPT)
+            update_trip<UPT>(a, pt, L.nodes, base, blockDim.x, ce, o, pol_stream, pol_keep);
+    }
 }
 
 // ---------------------------------------------------------------- modes 0 and 2
 
 // Block b runs lane lanes[b] = (graph rank, lane k) of iteration t.
-template <int UPT>
+template <int UPT, bool PIPE>
 __global__ void __launch_bounds__(256) batch_lane_kernel(BatchLaunch L, uint32_t max_paths, uint32_t t,
                                                          const uint2* __restrict__ lanes) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -202,7 +206,7 @@ __global__ void __launch_bounds__(256) batch_lane_kernel(BatchLaunch L, uint32_t
     const uint64_t pol_stream = policy_evict_first(), pol_keep = policy_evict_last();
     const uint32_t stride = G.max_active;
     for (uint32_t c = ln.y; c < G.n_chunks; c += stride)
-        run_chunk<UPT>(L, G, ln.x, s, zc, t, c, pol_stream, pol_keep);
+        run_chunk<UPT, PIPE>(L, G, ln.x, s, zc, t, c, pol_stream, pol_keep);
 }
 
 // ---------------------------------------------------------------- mode 1
@@ -274,7 +278,7 @@ __device__ __forceinline__ void complete_chunk(const BatchLaunch& L, const Batch
     }
 }
 
-template <int UPT>
+template <int UPT, bool PIPE>
 __global__ void __launch_bounds__(256) batch_persistent_kernel(BatchLaunch L, uint32_t max_paths, BatchQueues Q) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ ZipfConsts zc;
@@ -322,7 +326,7 @@ __global__ void __launch_bounds__(256) batch_persistent_kernel(BatchLaunch L, ui
                 __syncthreads();
                 cur = r;
             }
-            run_chunk<UPT>(L, G, r, s, zc, t, c, pol_stream, pol_keep);
+            run_chunk<UPT, PIPE>(L, G, r, s, zc, t, c, pol_stream, pol_keep);
             __threadfence();
             __syncthreads();
             if (threadIdx.x == 0) complete_chunk(L, Q, r, t);
@@ -363,6 +367,7 @@ struct BatchStress {
     uint64_t n_samples;
     uint32_t P;
     uint32_t key0, key1;
+    int pf64;                    // 64-byte L2 prefetch hint: bit 0 step loads, bit 1 node loads
     double* per_graph;           // [G][3]: sum, sum of squares, count
 };
 
@@ -392,12 +397,13 @@ __global__ void batch_stress_kernel(BatchStress L) {
         const uint64_t x = mulhi64(((uint64_t)w.w << 32) | (w.z & ~15u), n - 1);
         const uint64_t j = x + (x >= i);
         const uint32_t ei = w.z & 1u, ej = (w.z >> 1) & 1u;
-        const StepRec si = load_step(L.steps + off + i, pol_stream), sj = load_step(L.steps + off + j, pol_stream);
+        const StepRec si = load_step(L.steps + off + i, pol_stream, L.pf64 & 1);
+        const StepRec sj = load_step(L.steps + off + j, pol_stream, L.pf64 & 1);
         const int64_t pa = endpoint_pos(si, ei), pb = endpoint_pos(sj, ej);
         const int64_t d = pa > pb ? pa - pb : pb - pa;
         if (d == 0) continue;
-        const NodeRec na = load_node(L.nodes + step_node(si), pol_keep);
-        const NodeRec nb = load_node(L.nodes + step_node(sj), pol_keep);
+        const NodeRec na = load_node(L.nodes + step_node(si), pol_keep, L.pf64 & 2);
+        const NodeRec nb = load_node(L.nodes + step_node(sj), pol_keep, L.pf64 & 2);
         const float xa = ei ? na.ex : na.sx, ya = ei ? na.ey : na.sy;
         const float xb = ej ? nb.ex : nb.sx, yb = ej ? nb.ey : nb.sy;
         const float dx = __ll2float_rn((int64_t)si.ax - (int64_t)sj.ax) + (xa - xb);
@@ -494,6 +500,8 @@ struct pgsgd_batch {
     int timing = 0;
     int stall_test = 0;
     int blocks_per_sm = 0;
+    int pipeline = 0;
+    int pf64 = 7;
 
     // device state
     BatchGraph* d_graphs = nullptr;
@@ -614,37 +622,51 @@ int make_plan(uint32_t G, const uint64_t* n_updates, const uint64_t* n_nodes, in
     return PGSGD_OK;
 }
 
-template <int UPT>
+template <int UPT, bool PIPE>
 cudaError_t launch_lanes(const BatchLaunch& L, uint32_t max_paths, uint32_t t, const uint2* lanes, uint32_t n,
                          int block, size_t smem, cudaStream_t st) {
-    batch_lane_kernel<UPT><<<n, block, smem, st>>>(L, max_paths, t, lanes);
+    batch_lane_kernel<UPT, PIPE><<<n, block, smem, st>>>(L, max_paths, t, lanes);
     return cudaGetLastError();
 }
 
-cudaError_t launch_lanes_upt(int upt, const BatchLaunch& L, uint32_t max_paths, uint32_t t, const uint2* lanes,
-                             uint32_t n, int block, size_t smem, cudaStream_t st) {
+cudaError_t launch_lanes_upt(int upt, bool pipe, const BatchLaunch& L, uint32_t max_paths, uint32_t t,
+                             const uint2* lanes, uint32_t n, int block, size_t smem, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    if (upt == 1) return launch_lanes<1>(L, max_paths, t, lanes, n, block, smem, st);
-    if (upt == 4) return launch_lanes<4>(L, max_paths, t, lanes, n, block, smem, st);
-    return launch_lanes<2>(L, max_paths, t, lanes, n, block, smem, st);
+    if (pipe) {
+        if (upt == 1) return launch_lanes<1, true>(L, max_paths, t, lanes, n, block, smem, st);
+        if (upt == 4) return launch_lanes<4, true>(L, max_paths, t, lanes, n, block, smem, st);
+        return launch_lanes<2, true>(L, max_paths, t, lanes, n, block, smem, st);
+    }
+    if (upt == 1) return launch_lanes<1, false>(L, max_paths, t, lanes, n, block, smem, st);
+    if (upt == 4) return launch_lanes<4, false>(L, max_paths, t, lanes, n, block, smem, st);
+    return launch_lanes<2, false>(L, max_paths, t, lanes, n, block, smem, st);
 }
 
-template <int UPT>
-cudaError_t persistent_grid(int block, size_t smem, int sm_count, int per_sm_opt, int* grid) {
+template <int UPT, bool PIPE>
+cudaError_t persistent_launch(const BatchLaunch& L, uint32_t max_paths, const BatchQueues& Q, int block, size_t smem,
+                              int sm_count, int per_sm_opt, int* grid, cudaStream_t st) {
     int nb = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_persistent_kernel<UPT>, block, smem);
+    cudaError_t e =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_persistent_kernel<UPT, PIPE>, block, smem);
     if (e != cudaSuccess) return e;
     if (nb < 1) nb = 1;
     if (per_sm_opt > 0 && per_sm_opt < nb) nb = per_sm_opt;
     *grid = nb * sm_count;
-    return cudaSuccess;
+    batch_persistent_kernel<UPT, PIPE><<<*grid, block, smem, st>>>(L, max_paths, Q);
+    return cudaGetLastError();
 }
 
-template <int UPT>
-cudaError_t launch_persistent(const BatchLaunch& L, uint32_t max_paths, const BatchQueues& Q, int grid, int block,
-                              size_t smem, cudaStream_t st) {
-    batch_persistent_kernel<UPT><<<grid, block, smem, st>>>(L, max_paths, Q);
-    return cudaGetLastError();
+cudaError_t launch_persistent_upt(int upt, bool pipe, const BatchLaunch& L, uint32_t max_paths,
+                                  const BatchQueues& Q, int block, size_t smem, int sm_count, int per_sm_opt,
+                                  int* grid, cudaStream_t st) {
+    if (pipe) {
+        if (upt == 1) return persistent_launch<1, true>(L, max_paths, Q, block, smem, sm_count, per_sm_opt, grid, st);
+        if (upt == 4) return persistent_launch<4, true>(L, max_paths, Q, block, smem, sm_count, per_sm_opt, grid, st);
+        return persistent_launch<2, true>(L, max_paths, Q, block, smem, sm_count, per_sm_opt, grid, st);
+    }
+    if (upt == 1) return persistent_launch<1, false>(L, max_paths, Q, block, smem, sm_count, per_sm_opt, grid, st);
+    if (upt == 4) return persistent_launch<4, false>(L, max_paths, Q, block, smem, sm_count, per_sm_opt, grid, st);
+    return persistent_launch<2, false>(L, max_paths, Q, block, smem, sm_count, per_sm_opt, grid, st);
 }
 
 cudaError_t set_batch_smem(size_t smem) {
@@ -652,12 +674,18 @@ cudaError_t set_batch_smem(size_t smem) {
 #define PGSGD_ALLOW(k)                       \
     e = allow_smem(k, smem);                 \
     if (e != cudaSuccess) return e;
-    PGSGD_ALLOW(batch_lane_kernel<1>)
-    PGSGD_ALLOW(batch_lane_kernel<2>)
-    PGSGD_ALLOW(batch_lane_kernel<4>)
-    PGSGD_ALLOW(batch_persistent_kernel<1>)
-    PGSGD_ALLOW(batch_persistent_kernel<2>)
-    PGSGD_ALLOW(batch_persistent_kernel<4>)
+    PGSGD_ALLOW((batch_lane_kernel<1, false>))
+    PGSGD_ALLOW((batch_lane_kernel<2, false>))
+    PGSGD_ALLOW((batch_lane_kernel<4, false>))
+    PGSGD_ALLOW((batch_lane_kernel<1, true>))
+    PGSGD_ALLOW((batch_lane_kernel<2, true>))
+    PGSGD_ALLOW((batch_lane_kernel<4, true>))
+    PGSGD_ALLOW((batch_persistent_kernel<1, false>))
+    PGSGD_ALLOW((batch_persistent_kernel<2, false>))
+    PGSGD_ALLOW((batch_persistent_kernel<4, false>))
+    PGSGD_ALLOW((batch_persistent_kernel<1, true>))
+    PGSGD_ALLOW((batch_persistent_kernel<2, true>))
+    PGSGD_ALLOW((batch_persistent_kernel<4, true>))
     PGSGD_ALLOW(batch_debug_sample_kernel)
 #undef PGSGD_ALLOW
     return cudaSuccess;
@@ -878,6 +906,11 @@ int pgsgd_batch_set_option(pgsgd_batch* b, int option, int64_t v) {
         if (v < 0 || v > 32) return fail(PGSGD_EINVAL, "blocks per SM %lld not in 0..32", (long long)v);
         b->blocks_per_sm = (int)v;
         break;
+    case PGSGD_BOPT_PIPELINE: b->pipeline = v != 0; break;
+    case PGSGD_BOPT_PREFETCH64:
+        if (v < 0 || v > 15) return fail(PGSGD_EINVAL, "prefetch option %lld not in 0..15", (long long)v);
+        b->pf64 = (int)v;
+        break;
     default: return fail(PGSGD_EINVAL, "unknown batch option %d", option);
     }
     return PGSGD_OK;
@@ -897,6 +930,8 @@ int pgsgd_batch_get_option(const pgsgd_batch* b, int option, int64_t* v) {
     case PGSGD_BOPT_TIMING: *v = b->timing; break;
     case PGSGD_BOPT_STALL_TEST: *v = b->stall_test; break;
     case PGSGD_BOPT_BLOCKS_PER_SM: *v = b->blocks_per_sm; break;
+    case PGSGD_BOPT_PIPELINE: *v = b->pipeline; break;
+    case PGSGD_BOPT_PREFETCH64: *v = b->pf64; break;
     default: return fail(PGSGD_EINVAL, "unknown batch option %d", option);
     }
     return PGSGD_OK;
@@ -1041,7 +1076,7 @@ int pgsgd_batch_layout(pgsgd_batch* b, uint32_t iter_max, const double* eta, dou
     L.iter_end = iter_end;
     L.theta = th;
     L.store_mode = 1;
-    L.pf64 = 3;
+    L.pf64 = b->pf64 & 3;
     L.timeout_ns = (uint64_t)b->timeout_ms * 1000000ull;
     const size_t smem = batch_smem_bytes(b->max_paths);
     const uint32_t n_lanes = b->lane_start[G];
@@ -1078,35 +1113,31 @@ int pgsgd_batch_layout(pgsgd_batch* b, uint32_t iter_max, const double* eta, dou
         BCK(cudaMemcpyAsync(b->d_misc, misc, 8, cudaMemcpyHostToDevice, st), "queue upload");
         BatchQueues Q{b->d_q, b->d_done, b->d_misc, b->d_misc + 1};
         int grid = 0;
-        cudaError_t e;
-        if (b->upt == 1) e = persistent_grid<1>(b->block, smem, b->g->sm_count, b->blocks_per_sm, &grid);
-        else if (b->upt == 4) e = persistent_grid<4>(b->block, smem, b->g->sm_count, b->blocks_per_sm, &grid);
-        else e = persistent_grid<2>(b->block, smem, b->g->sm_count, b->blocks_per_sm, &grid);
-        BCK(e, "occupancy");
-        if (b->upt == 1) e = launch_persistent<1>(L, b->max_paths, Q, grid, b->block, smem, st);
-        else if (b->upt == 4) e = launch_persistent<4>(L, b->max_paths, Q, grid, b->block, smem, st);
-        else e = launch_persistent<2>(L, b->max_paths, Q, grid, b->block, smem, st);
+        const cudaError_t e = launch_persistent_upt(b->upt, b->pipeline != 0, L, b->max_paths, Q, b->block, smem,
+                                                    b->g->sm_count, b->blocks_per_sm, &grid, st);
         BCK(e, "persistent batch kernel");
         b->last_grid = grid;
         launches = 1;
     } else {
         const bool capture = b->cuda_graph != 0;
         char key[256];
-        snprintf(key, sizeof key, "%d/%u/%u/%u/%d/%d/%lld/%.9g/%p/%p/%u", b->mode, iter_max, iter_begin, iter_end,
-                 b->block, b->upt, (long long)b->chunk, (double)th, (void*)b->d_eta, (void*)b->d_lanes, n_lanes);
+        snprintf(key, sizeof key, "%d/%u/%u/%u/%d/%d/%lld/%.9g/%p/%p/%u/%d/%d", b->mode, iter_max, iter_begin,
+                 iter_end, b->block, b->upt, (long long)b->chunk, (double)th, (void*)b->d_eta, (void*)b->d_lanes,
+                 n_lanes, b->pipeline, b->pf64);
         // the lane table and per-rank lane ranges are part of the replayed work
         std::string k2 = key;
         for (uint32_t r = 0; r <= G; ++r) k2 += "," + std::to_string(b->lane_start[r]);
         auto enqueue = [&](cudaStream_t s) -> cudaError_t {
             for (uint32_t t = iter_begin; t < iter_end; ++t) {
                 if (b->mode == 0) {
-                    cudaError_t e = launch_lanes_upt(b->upt, L, b->max_paths, t, b->d_lanes, n_lanes, b->block, smem, s);
+                    cudaError_t e = launch_lanes_upt(b->upt, b->pipeline != 0, L, b->max_paths, t, b->d_lanes, n_lanes,
+                                                     b->block, smem, s);
                     if (e != cudaSuccess) return e;
                 } else {
                     for (uint32_t r = 0; r < G; ++r) {
                         const uint32_t n = b->lane_start[r + 1] - b->lane_start[r];
-                        cudaError_t e = launch_lanes_upt(b->upt, L, b->max_paths, t, b->d_lanes + b->lane_start[r], n,
-                                                         b->block, smem, s);
+                        cudaError_t e = launch_lanes_upt(b->upt, b->pipeline != 0, L, b->max_paths, t,
+                                                         b->d_lanes + b->lane_start[r], n, b->block, smem, s);
                         if (e != cudaSuccess) return e;
                     }
                 }
@@ -1221,6 +1252,7 @@ int pgsgd_batch_stress(pgsgd_batch* b, uint32_t samples_per_step, uint64_t seed,
         L.P = P;
         L.key0 = (uint32_t)seed;
         L.key1 = (uint32_t)(seed >> 32);
+        L.pf64 = (b->pf64 >> 2) & 3;
         L.per_graph = b->d_per_graph;
         const uint64_t want = (n_samples + 255) / 256;
         const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)b->g->sm_count * 16));

@@ -438,53 +438,66 @@ struct UpdateOpts {
     bool atomic;     // add the moves atomically instead of replacing the points
 };
 
-// UPT independent updates u0 + k * stride (k < UPT, only those below u_end)
-// of Algorithm 1, lines 5-15, kept in flight together: all draws first (ALU),
-// then all step-record loads, then all node-record loads, then the moves.
+// The pairs of UPT independent updates u0 + k * stride (k < UPT; only those
+// below u_end are active) of Algorithm 1, lines 5-11.
 template <int UPT>
-__device__ __forceinline__ void update_trip(const SamplerArgs& a, const PathTable& pt, NodeRec* __restrict__ nodes,
-                                            uint64_t u0, uint64_t stride, uint64_t u_end, const UpdateOpts& o,
-                                            uint64_t pol_stream, uint64_t pol_keep) {
-    const StepRec* __restrict__ steps = a.steps;
-    uint64_t gi[UPT], gj[UPT];
-    uint32_t w2[UPT];
+struct TripDraws {
+    uint64_t gi[UPT], gj[UPT];  // global step indices of n_i and n_j
+    uint32_t w2[UPT];           // coin word (endpoint bits 2 and 3)
     bool act[UPT];
+};
+
+template <int UPT>
+__device__ __forceinline__ void draw_trip(const SamplerArgs& a, const PathTable& pt, uint64_t u0, uint64_t stride,
+                                          uint64_t u_end, TripDraws<UPT>& d) {
 #pragma unroll
     for (int k = 0; k < UPT; ++k) {
         const uint64_t u = u0 + (uint64_t)k * stride;
-        act[k] = u < u_end;
-        if (act[k]) {
+        d.act[k] = u < u_end;
+        if (d.act[k]) {
             const Pair pr = draw_pair(a, pt, u);
-            act[k] = !pr.short_path;
-            gi[k] = pr.base + pr.i;
-            gj[k] = pr.base + pr.j;
-            w2[k] = pr.w2;
+            d.act[k] = !pr.short_path;
+            d.gi[k] = pr.base + pr.i;
+            d.gj[k] = pr.base + pr.j;
+            d.w2[k] = pr.w2;
         }
     }
-    StepRec si[UPT], sj[UPT];
+}
+
+template <int UPT>
+__device__ __forceinline__ void load_trip_steps(const StepRec* __restrict__ steps, const TripDraws<UPT>& d,
+                                                StepRec (&si)[UPT], StepRec (&sj)[UPT], uint64_t pol_stream,
+                                                int pf64) {
 #pragma unroll
     for (int k = 0; k < UPT; ++k) {
-        if (act[k]) {
-            si[k] = load_step(steps + gi[k], pol_stream, o.pf64 & 1);
-            sj[k] = load_step(steps + gj[k], pol_stream, o.pf64 & 1);
+        if (d.act[k]) {
+            si[k] = load_step(steps + d.gi[k], pol_stream, pf64 & 1);
+            sj[k] = load_step(steps + d.gj[k], pol_stream, pf64 & 1);
         }
     }
+}
+
+// Node-record loads, the moves of Algorithm 1, lines 12-15, and the stores.
+template <int UPT>
+__device__ __forceinline__ void finish_trip(NodeRec* __restrict__ nodes, const TripDraws<UPT>& d,
+                                            const StepRec (&si)[UPT], const StepRec (&sj)[UPT], const UpdateOpts& o,
+                                            uint64_t pol_keep) {
     NodeRec na[UPT], nb[UPT];
 #pragma unroll
     for (int k = 0; k < UPT; ++k) {
-        if (act[k]) {
+        if (d.act[k]) {
             na[k] = load_node(nodes + step_node(si[k]), pol_keep, o.pf64 & 2);
             nb[k] = load_node(nodes + step_node(sj[k]), pol_keep, o.pf64 & 2);
         }
     }
 #pragma unroll
     for (int k = 0; k < UPT; ++k) {
-        if (!act[k]) continue;
-        const uint32_t ea = (w2[k] >> 2) & 1u, eb = (w2[k] >> 3) & 1u;
+        if (!d.act[k]) continue;
+        const uint32_t ea = (d.w2[k] >> 2) & 1u, eb = (d.w2[k] >> 3) & 1u;
         const int64_t pa = endpoint_pos(si[k], ea), pb = endpoint_pos(sj[k], eb);
-        const int64_t d = pa > pb ? pa - pb : pb - pa;
-        if (d == 0) continue;
-        const Move m = pair_move(na[k], si[k].ax, ea, nb[k], sj[k].ax, eb, d, o.eta);
+        const int64_t dd = pa > pb ? pa - pb : pb - pa;
+        if (dd == 0) continue;
+        const Move m = pair_move(na[k], si[k].ax, ea, nb[k], sj[k].ax, eb, dd, o.eta);
         if (!m.moved) continue;
         float* pa_ptr = &nodes[step_node(si[k])].sx + 2 * ea;
         float* pb_ptr = &nodes[step_node(sj[k])].sx + 2 * eb;
@@ -505,4 +518,38 @@ __device__ __forceinline__ void update_trip(const SamplerArgs& a, const PathTabl
     }
 }
 
+// UPT independent updates kept in flight together: all draws first (ALU),
+// then all step-record loads, then all node-record loads, then the moves.
+template <int UPT>
+__device__ __forceinline__ void update_trip(const SamplerArgs& a, const PathTable& pt, NodeRec* __restrict__ nodes,
+                                            uint64_t u0, uint64_t stride, uint64_t u_end, const UpdateOpts& o,
+                                            uint64_t pol_stream, uint64_t pol_keep) {
+    TripDraws<UPT> d;
+    draw_trip<UPT>(a, pt, u0, stride, u_end, d);
+    StepRec si[UPT], sj[UPT];
+    load_trip_steps<UPT>(a.steps, d, si, sj, pol_stream, o.pf64);
+    finish_trip<UPT>(nodes, d, si, sj, o, pol_keep);
+}
+
+// The updates u_first + m * stride < u_end, UPT per trip, software
+// pipelined: a trip's step-record loads are issued before the next trip's
+// pairs are drawn, so the sampler's arithmetic overlaps the loads' latency.
+// The same updates, draws and moves as update_trip over the same range.
+template <int UPT>
+__device__ __forceinline__ void update_range_pipelined(const SamplerArgs& a, const PathTable& pt,
+                                                       NodeRec* __restrict__ nodes, uint64_t u_first, uint64_t stride,
+                                                       uint64_t u_end, const UpdateOpts& o, uint64_t pol_stream,
+                                                       uint64_t pol_keep) {
+    const uint64_t trip = stride * UPT;
+    TripDraws<UPT> cur;
+    draw_trip<UPT>(a, pt, u_first, stride, u_end, cur);
+    for (uint64_t base = u_first; base < u_end; base += trip) {
+        StepRec si[UPT], sj[UPT];
+        load_trip_steps<UPT>(a.steps, cur, si, sj, pol_stream, o.pf64);
+        TripDraws<UPT> nxt;
+        draw_trip<UPT>(a, pt, base + trip, stride, u_end, nxt);
+        finish_trip<UPT>(nodes, cur, si, sj, o, pol_keep);
+        cur = nxt;
+    }
+}
 }  // namespace pgsgd

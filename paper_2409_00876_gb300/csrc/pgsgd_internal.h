@@ -39,6 +39,7 @@ struct UpdateLaunch {
     bool l2_hints;       // evict-first step records, evict-last node records
     int pf64;            // 64-byte L2 prefetch hint: bit 0 step loads, bit 1 node loads
     bool atomic;
+    bool pipeline;       // software-pipelined update loop
 };
 
 struct StressLaunch {
@@ -52,6 +53,7 @@ struct StressLaunch {
     double* partials;           // [grid][3]
     double* per_path;           // [P][3] or nullptr
     int block, grid;
+    int pf64;                   // 64-byte L2 prefetch hint: bit 0 step loads, bit 1 node loads
 };
 
 // Shared memory of the staged path tables (offsets, Zipf thresholds, Zipf B, guide).
@@ -148,7 +150,8 @@ struct pgsgd_graph {
     int l2_fetch = 0;
     int store_mode = 1;  // 64-bit atomic exchange: measured fastest replace-store
     int l2_hints = 1;
-    int pf64 = 3;
+    int pf64 = 7;
+    int pipeline = 0;
 
     // timing
     std::vector<cudaEvent_t> ev_free;

@@ -178,8 +178,10 @@ __global__ void zipf_setup_kernel(const uint64_t* __restrict__ path_off, uint32_
 // ---------------------------------------------------------------- the update kernel
 
 // One launch = one iteration's N updates (or a slice), grid-stride over the
-// update index u; every loop trip is one update_trip of UPT updates.
-template <int UPT, int MINB>
+// update index u; every loop trip is one update_trip of UPT updates (PIPE:
+// the software-pipelined loop, drawing the next trip while this trip's step
+// records load).
+template <int UPT, int MINB, bool PIPE>
 __global__ void __launch_bounds__(256, MINB) update_kernel(UpdateLaunch L) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ ZipfConsts zc;
@@ -192,8 +194,12 @@ __global__ void __launch_bounds__(256, MINB) update_kernel(UpdateLaunch L) {
     const uint64_t gtid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     const UpdateOpts o{L.eta, L.store_mode, L.pf64, L.atomic};
     const uint64_t u_end = L.u_begin + L.n_updates;
-    for (uint64_t base = L.u_begin + gtid; base < u_end; base += nthr * UPT)
-        update_trip<UPT>(a, pt, L.nodes, base, nthr, u_end, o, pol_stream, pol_keep);
+    if (PIPE) {
+        update_range_pipelined<UPT>(a, pt, L.nodes, L.u_begin + gtid, nthr, u_end, o, pol_stream, pol_keep);
+    } else {
+        for (uint64_t base = L.u_begin + gtid; base < u_end; base += nthr * UPT)
+            update_trip<UPT>(a, pt, L.nodes, base, nthr, u_end, o, pol_stream, pol_keep);
+    }
 }
 
 // ---------------------------------------------------------------- debug kernels
@@ -293,15 +299,15 @@ __global__ void stress_kernel(StressLaunch L) {
             const uint64_t j = x + (x >= i);
             ei[k] = w.z & 1u;
             ej[k] = (w.z >> 1) & 1u;
-            si[k] = load_step(L.steps + off + i, pol_stream);
-            sj[k] = load_step(L.steps + off + j, pol_stream);
+            si[k] = load_step(L.steps + off + i, pol_stream, L.pf64 & 1);
+            sj[k] = load_step(L.steps + off + j, pol_stream, L.pf64 & 1);
         }
         NodeRec na[SPT], nb[SPT];
 #pragma unroll
         for (int k = 0; k < SPT; ++k) {
             if (!act[k]) continue;
-            na[k] = load_node(L.nodes + step_node(si[k]), pol_keep);
-            nb[k] = load_node(L.nodes + step_node(sj[k]), pol_keep);
+            na[k] = load_node(L.nodes + step_node(si[k]), pol_keep, L.pf64 & 2);
+            nb[k] = load_node(L.nodes + step_node(sj[k]), pol_keep, L.pf64 & 2);
         }
 #pragma unroll
         for (int k = 0; k < SPT; ++k) {
@@ -462,13 +468,13 @@ cudaError_t launch_zipf_setup(const uint64_t* path_off, uint32_t n_paths, float 
     return cudaGetLastError();
 }
 
-template <int UPT, int MINB>
+template <int UPT, int MINB, bool PIPE = false>
 static cudaError_t launch_update_t(const UpdateLaunch& L, cudaStream_t st) {
     const size_t smem = update_smem_bytes(L.s.n_paths, L.s.n_guide);
-    cudaError_t e = cudaFuncSetAttribute(update_kernel<UPT, MINB>,
+    cudaError_t e = cudaFuncSetAttribute(update_kernel<UPT, MINB, PIPE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    update_kernel<UPT, MINB><<<L.grid, L.block, smem, st>>>(L);
+    update_kernel<UPT, MINB, PIPE><<<L.grid, L.block, smem, st>>>(L);
     return cudaGetLastError();
 }
 
@@ -476,6 +482,16 @@ static cudaError_t launch_update_t(const UpdateLaunch& L, cudaStream_t st) {
 // SM the register allocation must allow (1 = unconstrained).
 cudaError_t launch_update(const UpdateLaunch& L, cudaStream_t st) {
     if (L.n_updates == 0) return cudaSuccess;
+    if (L.pipeline) {
+        switch (L.upt * 10 + L.minb) {
+            case 11: return launch_update_t<1, 1, true>(L, st);
+            case 13: return launch_update_t<1, 3, true>(L, st);
+            case 21: return launch_update_t<2, 1, true>(L, st);
+            case 22: return launch_update_t<2, 2, true>(L, st);
+            case 41: return launch_update_t<4, 1, true>(L, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (L.upt * 10 + L.minb) {
         case 11: return launch_update_t<1, 1>(L, st);
         case 14: return launch_update_t<1, 4>(L, st);
