@@ -68,6 +68,12 @@ def _L():
             lib.orc_zipf_sample.argtypes = [dbl, u64, u64, u64, P]
             lib.orc_sample.argtypes = gargs + [u32, u32, dbl, u64, u64, u64, P]
             lib.orc_sample.restype = i32
+            lib.orc_sample_wm.argtypes = gargs + [u32, u32, dbl, u64, i32, u64, u64, P]
+            lib.orc_sample_wm.restype = i32
+            lib.orc_sample_reuse.argtypes = gargs + [u32, u32, dbl, u64, i32, u32, u64, u64, u64, P]
+            lib.orc_sample_reuse.restype = i32
+            lib.orc_layout_variant.argtypes = gargs + [P, u32, P, dbl, u64, u32, u32, u64, i32, u32, P]
+            lib.orc_layout_variant.restype = i32
             lib.orc_eta_schedule.argtypes = [u32, dbl, dbl, P]
             lib.orc_sweep.argtypes = gargs + [P, u32, u32, dbl, dbl, u64, u64, u64, P]
             lib.orc_sweep.restype = i32
@@ -171,6 +177,52 @@ def sample(g, T, t, theta, seed, u_begin, count) -> np.ndarray:
     if rc:
         raise MemoryError("oracle sample")
     return out
+
+
+def sample_wm(g, T, t, theta, seed, u_begin, count, wm=1) -> np.ndarray:
+    """As sample, with the cooling coin of every update taken from its group of 32 (warp merging)."""
+    out = np.zeros(count, dtype=SAMPLE_DTYPE)
+    rc = _L().orc_sample_wm(*_ga(g).args(), int(T), int(t), float(theta), int(seed), int(wm),
+                            int(u_begin), int(count), _ptr(out))
+    if rc:
+        raise MemoryError("oracle sample")
+    return out
+
+
+def sample_reuse(g, T, t, theta, seed, drf, n_sel, q_begin, count, wm=0) -> np.ndarray:
+    """The drf pairs of every selection q in [q_begin, q_begin + count) under
+    warp-level data reuse: [count, drf] records (round k in column k)."""
+    out = np.zeros(count * drf, dtype=SAMPLE_DTYPE)
+    rc = _L().orc_sample_reuse(*_ga(g).args(), int(T), int(t), float(theta), int(seed), int(wm),
+                               int(drf), int(n_sel), int(q_begin), int(count), _ptr(out))
+    if rc:
+        raise MemoryError("oracle sample")
+    return out.reshape(count, drf)
+
+
+def n_selections(g, updates_per_step=10, srf=1) -> int:
+    """Selections per iteration with step reduction factor srf."""
+    return -(-updates_per_step * g.n_steps // srf)
+
+
+def layout_variant(g, xy, T=30, eta=None, theta=0.99, seed=1, t_begin=0, t_end=None, drf=1, srf=1,
+                   wm=0, updates_per_step=10, n_units=None):
+    """Sequential Algorithm 1 under warp merging (wm) and data reuse (drf, srf);
+    drf = srf = 1, wm = 0 is layout(..., n_threads=1). Returns (new xy, moves)."""
+    xy = np.array(xy, dtype=np.float64, order="C", copy=True)
+    if eta is None:
+        eta = eta_schedule(T, default_eta_max(g))
+    eta = np.ascontiguousarray(eta, dtype=np.float64)
+    if t_end is None:
+        t_end = T
+    if n_units is None:
+        n_units = n_selections(g, updates_per_step, srf)
+    moved = C.c_uint64()
+    rc = _L().orc_layout_variant(*_ga(g).args(), _ptr(xy), int(T), _ptr(eta), float(theta), int(seed),
+                                 int(t_begin), int(t_end), int(n_units), int(wm), int(drf), C.byref(moved))
+    if rc:
+        raise MemoryError("oracle layout")
+    return xy, moved.value
 
 
 def sweep(g, xy, T, t, eta, theta, seed, u_begin, count) -> np.ndarray:

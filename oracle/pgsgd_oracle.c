@@ -358,7 +358,38 @@ static int64_t endpoint_pos(const orc_graph *G, uint64_t step, int e)
     return pos + (((e ^ rev) & 1) ? len : 0);
 }
 
-static void sample_update(const sampler_t *S, uint32_t t, uint64_t u, orc_sample_rec *r)
+/* Partner step j of step i on path p (n >= 2 steps) from the words w of   */
+/* block 0 of counter (c0, c1, t) (Algorithm 1, lines 6-11).                */
+static uint64_t partner_step(const sampler_t *S, uint32_t p, uint64_t n, uint64_t i, int cooling,
+                             const uint32_t w[4], uint32_t c0, uint32_t c1, uint32_t t)
+{
+    if (cooling) {
+        uint64_t k = zipf_draw(&S->zipf[p], w[3], S->seed, c0, c1, t);
+        int fwd = (w[2] >> 1) & 1u;
+        int can_fwd = i + k < n, can_bwd = i >= k;
+        if (fwd && can_fwd) return i + k;
+        if (!fwd && can_bwd) return i - k;
+        if (can_fwd) return i + k;
+        if (can_bwd) return i - k;
+        return (n - 1 - i > i) ? n - 1 : 0;
+    }
+    uint64_t x = mulhi64(((uint64_t)w[3] << 32) | (w[2] & ~15u), n - 1);
+    return x + (x >= i);
+}
+
+/* Warp merging (Section V-B3): one control draw decides the branch for a  */
+/* group of 32 consecutive updates. Reading: the cooling coin of update u   */
+/* is bit 0 of w2 of update 32 floor(u / 32).                               */
+static int group_coin(const sampler_t *S, uint32_t t, uint64_t u)
+{
+    uint64_t u0 = u & ~(uint64_t)31;
+    uint32_t w[4];
+    philox_block(S->seed, (uint32_t)u0, (uint32_t)(u0 >> 32), t, 0u, w);
+    return (int)(w[2] & 1u);
+}
+
+/* Update u of iteration t; wm = 1 takes the cooling coin of its group.     */
+static void sample_update_coin(const sampler_t *S, uint32_t t, uint64_t u, int wm, orc_sample_rec *r)
 {
     const orc_graph *G = S->G;
     uint32_t c0 = (uint32_t)u, c1 = (uint32_t)(u >> 32);
@@ -370,31 +401,24 @@ static void sample_update(const sampler_t *S, uint32_t t, uint64_t u, orc_sample
     uint64_t off = G->path_off[p];
     uint64_t n = G->path_off[p + 1] - off;
     uint64_t i = g - off;
+    int coin = wm ? group_coin(S, t, u) : (int)(w[2] & 1u);
     memset(r, 0, sizeof *r);
     r->g = g; r->path = p; r->i = i;
-    r->cooling = (2ull * t >= S->T) || (w[2] & 1u);
+    r->cooling = (2ull * t >= S->T) || coin;
     r->e_i = (w[2] >> 2) & 1u;
     r->e_j = (w[2] >> 3) & 1u;
     if (n < 2) { r->skip = 1; r->j = i; return; }
-    uint64_t j;
-    if (r->cooling) {
-        uint64_t k = zipf_draw(&S->zipf[p], w[3], S->seed, c0, c1, t);
-        int fwd = (w[2] >> 1) & 1u;
-        int can_fwd = i + k < n, can_bwd = i >= k;
-        if (fwd && can_fwd) j = i + k;
-        else if (!fwd && can_bwd) j = i - k;
-        else if (can_fwd) j = i + k;
-        else if (can_bwd) j = i - k;
-        else j = (n - 1 - i > i) ? n - 1 : 0;
-    } else {
-        uint64_t x = mulhi64(((uint64_t)w[3] << 32) | (w[2] & ~15u), n - 1);
-        j = x + (x >= i);
-    }
+    uint64_t j = partner_step(S, p, n, i, r->cooling, w, c0, c1, t);
     r->j = j;
     int64_t a = endpoint_pos(G, off + i, r->e_i);
     int64_t b = endpoint_pos(G, off + j, r->e_j);
     r->d_ref = a > b ? a - b : b - a;
     if (r->d_ref == 0) r->skip = 2;
+}
+
+static void sample_update(const sampler_t *S, uint32_t t, uint64_t u, orc_sample_rec *r)
+{
+    sample_update_coin(S, t, u, 0, r);
 }
 
 static int sampler_init(sampler_t *S, const orc_graph *G, uint32_t T, double theta, uint64_t seed)
@@ -566,6 +590,179 @@ int orc_layout(GRAPH_ARGS, double *xy, uint32_t T, const double *eta, double the
     }
     if (moved_out) *moved_out = moved;
     free(jobs); free(th);
+    sampler_free(&S);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Warp-level data reuse (Section VII-D) and warp merging, sequential.  */
+/* Readings (the paper forms new pairs by shuffling cached node data in */
+/* a warp but does not say how their reference distance is defined; it  */
+/* exists only for two steps of one path):                               */
+/*  - an iteration has n_sel selections; the 32 selections of group      */
+/*    G = floor(q / 32) share one path, drawn in proportion to |p| from  */
+/*    block 0 of counter (G_lo, G_hi, t, 0x20000000): g = mulhi64(w0 |   */
+/*    w1 << 32, S);                                                      */
+/*  - selection q draws, from block 0 of its own counter (q_lo, q_hi, t, */
+/*    0), its step i = mulhi64(w0 | w1 << 32, n_p), its coins and its    */
+/*    partner j exactly as an update does (the group's cooling coin with */
+/*    warp merging);                                                     */
+/*  - with data reuse factor r, round k = 0..r-1 of lane l = q mod 32    */
+/*    pairs (i, e_i) of lane l with (j, e_j) of lane m = (l + o_k) mod   */
+/*    32, o_0 = 0, o_k = 1 + floor(31 w / 2^32) for the (k-1)-th word of */
+/*    blocks 1, 2 of the group counter; a pair whose partner selection   */
+/*    does not exist or whose path has < 2 steps is skipped;             */
+/*  - order: groups in order, rounds in order, lanes in order, each      */
+/*    update applied at once (a Gauss-Seidel reading of the warp's       */
+/*    simultaneous round).                                               */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    uint64_t i, j;
+    uint8_t cooling, e_i, e_j, valid;
+} sel_t;
+
+static uint32_t group_path(const sampler_t *S, uint32_t t, uint64_t grp)
+{
+    uint32_t w[4];
+    philox_block(S->seed, (uint32_t)grp, (uint32_t)(grp >> 32), t, 0x20000000u, w);
+    uint64_t steps = S->G->path_off[S->G->n_paths];
+    return find_path(S->G, mulhi64((uint64_t)w[0] | ((uint64_t)w[1] << 32), steps));
+}
+
+static uint32_t reuse_offset(const sampler_t *S, uint32_t t, uint64_t grp, uint32_t k)
+{
+    if (k == 0) return 0;
+    uint32_t idx = k - 1, w[4];
+    philox_block(S->seed, (uint32_t)grp, (uint32_t)(grp >> 32), t, 0x20000000u | (1u + idx / 4), w);
+    return 1u + (uint32_t)(((uint64_t)w[idx % 4] * 31u) >> 32);
+}
+
+static void sample_selection(const sampler_t *S, uint32_t t, uint64_t q, int wm, uint32_t p, sel_t *r)
+{
+    const orc_graph *G = S->G;
+    uint32_t c0 = (uint32_t)q, c1 = (uint32_t)(q >> 32);
+    uint32_t w[4];
+    philox_block(S->seed, c0, c1, t, 0u, w);
+    uint64_t n = G->path_off[p + 1] - G->path_off[p];
+    int coin = wm ? group_coin(S, t, q) : (int)(w[2] & 1u);
+    memset(r, 0, sizeof *r);
+    r->cooling = (2ull * t >= S->T) || coin;
+    r->e_i = (w[2] >> 2) & 1u;
+    r->e_j = (w[2] >> 3) & 1u;
+    if (n < 2) return;
+    r->i = mulhi64((uint64_t)w[0] | ((uint64_t)w[1] << 32), n);
+    r->j = partner_step(S, p, n, r->i, r->cooling, w, c0, c1, t);
+    r->valid = 1;
+}
+
+/* The pairs of updates [u_begin, u_begin + count) with warp merging.       */
+int orc_sample_wm(GRAPH_ARGS, uint32_t T, uint32_t t, double theta, uint64_t seed, int wm,
+                  uint64_t u_begin, uint64_t count, orc_sample_rec *out)
+{
+    GRAPH_INIT;
+    sampler_t S;
+    if (sampler_init(&S, &G, T, theta, seed)) return -1;
+    for (uint64_t q = 0; q < count; ++q) sample_update_coin(&S, t, u_begin + q, wm, &out[q]);
+    sampler_free(&S);
+    return 0;
+}
+
+/* The r pairs of every selection q in [q_begin, q_begin + count) of an     */
+/* iteration with n_sel selections: out[(q - q_begin) r + k] for round k.    */
+/* g = the global step of i; cooling is that of the partner lane's draw.     */
+int orc_sample_reuse(GRAPH_ARGS, uint32_t T, uint32_t t, double theta, uint64_t seed, int wm,
+                     uint32_t drf, uint64_t n_sel, uint64_t q_begin, uint64_t count,
+                     orc_sample_rec *out)
+{
+    GRAPH_INIT;
+    sampler_t S;
+    if (sampler_init(&S, &G, T, theta, seed)) return -1;
+    for (uint64_t c = 0; c < count; ++c) {
+        uint64_t q = q_begin + c, grp = q >> 5;
+        uint32_t lane = (uint32_t)(q & 31), p = group_path(&S, t, grp);
+        uint64_t off = G.path_off[p];
+        sel_t mine;
+        sample_selection(&S, t, q, wm, p, &mine);
+        for (uint32_t k = 0; k < drf; ++k) {
+            uint64_t qm = (grp << 5) | ((lane + reuse_offset(&S, t, grp, k)) & 31u);
+            sel_t other;
+            sample_selection(&S, t, qm, wm, p, &other);
+            orc_sample_rec *r = &out[c * drf + k];
+            memset(r, 0, sizeof *r);
+            r->g = off + mine.i; r->i = mine.i; r->j = other.j; r->path = p;
+            r->cooling = other.cooling; r->e_i = mine.e_i; r->e_j = other.e_j;
+            if (!(mine.valid && other.valid && q < n_sel && qm < n_sel)) { r->skip = 1; continue; }
+            int64_t a = endpoint_pos(&G, off + mine.i, mine.e_i);
+            int64_t b = endpoint_pos(&G, off + other.j, other.e_j);
+            r->d_ref = a > b ? a - b : b - a;
+            if (r->d_ref == 0) r->skip = 2;
+        }
+    }
+    sampler_free(&S);
+    return 0;
+}
+
+static int apply_pair(const orc_graph *G, double *xy, uint64_t si, int ei, uint64_t sj, int ej,
+                      int64_t d, double eta)
+{
+    uint32_t ni = G->step_node[si], nj = G->step_node[sj];
+    double *pi = xy + 4 * (uint64_t)ni + 2 * ei;
+    double *pj = xy + 4 * (uint64_t)nj + 2 * ej;
+    double vi[2] = {pi[0], pi[1]}, vj[2] = {pj[0], pj[1]}, dl[4];
+    int moved;
+    update_delta(vi, vj, (double)d, eta, dl, &moved);
+    if (!moved) return 0;
+    pi[0] = vi[0] + dl[0]; pi[1] = vi[1] + dl[1];
+    pj[0] = vj[0] + dl[2]; pj[1] = vj[1] + dl[3];
+    return 1;
+}
+
+/* Iterations [t_begin, t_end), sequential. drf = 1: n_units updates of the */
+/* standard sampler (group coin with wm); drf > 1: n_units selections with  */
+/* data reuse factor drf (the readings above).                              */
+int orc_layout_variant(GRAPH_ARGS, double *xy, uint32_t T, const double *eta, double theta,
+                       uint64_t seed, uint32_t t_begin, uint32_t t_end, uint64_t n_units, int wm,
+                       uint32_t drf, uint64_t *moved_out)
+{
+    GRAPH_INIT;
+    sampler_t S;
+    if (sampler_init(&S, &G, T, theta, seed)) return -1;
+    uint64_t moved = 0;
+    sel_t sel[32];
+    for (uint32_t t = t_begin; t < t_end; ++t) {
+        if (drf <= 1) {
+            for (uint64_t u = 0; u < n_units; ++u) {
+                orc_sample_rec r;
+                sample_update_coin(&S, t, u, wm, &r);
+                if (r.skip) continue;
+                uint64_t off = G.path_off[r.path];
+                moved += apply_pair(&G, xy, off + r.i, r.e_i, off + r.j, r.e_j, r.d_ref, eta[t]);
+            }
+            continue;
+        }
+        for (uint64_t grp = 0; grp << 5 < n_units; ++grp) {
+            uint32_t p = group_path(&S, t, grp);
+            uint64_t off = G.path_off[p];
+            for (uint32_t l = 0; l < 32; ++l) {
+                uint64_t q = (grp << 5) | l;
+                sample_selection(&S, t, q, wm, p, &sel[l]);
+                if (q >= n_units) sel[l].valid = 0;
+            }
+            for (uint32_t k = 0; k < drf; ++k) {
+                uint32_t o = reuse_offset(&S, t, grp, k);
+                for (uint32_t l = 0; l < 32; ++l) {
+                    const sel_t *a = &sel[l], *b = &sel[(l + o) & 31u];
+                    if (!a->valid || !b->valid) continue;
+                    int64_t pa = endpoint_pos(&G, off + a->i, a->e_i), pb = endpoint_pos(&G, off + b->j, b->e_j);
+                    int64_t d = pa > pb ? pa - pb : pb - pa;
+                    if (d == 0) continue;
+                    moved += apply_pair(&G, xy, off + a->i, a->e_i, off + b->j, b->e_j, d, eta[t]);
+                }
+            }
+        }
+    }
+    if (moved_out) *moved_out = moved;
     sampler_free(&S);
     return 0;
 }
