@@ -109,7 +109,24 @@ typedef enum pgsgd_option {
      * step-record loads, then draws the next trip's pairs while they are in
      * flight (same draws and moves; compiled for updates per thread / min
      * blocks 1/1, 1/3, 2/1, 2/2 and 4/1). Default 0. */
-    PGSGD_OPT_PIPELINE = 15
+    PGSGD_OPT_PIPELINE = 15,
+    /* Warp merging (Section V-B3): 1 = the cooling coin of update u is bit 0
+     * of w2 of update 32 floor(u / 32), so a warp's 32 consecutive updates
+     * take the same branch (one control draw, shared by shuffle). Draws and
+     * moves otherwise unchanged. Default 0. */
+    PGSGD_OPT_WARP_MERGE = 16,
+    /* Warp-level data reuse (Section VII-D). Data reuse factor DRF (1, 2, 4
+     * or 8; default 1 = off): every selection performs DRF updates; the 32
+     * selections of a group (= a warp) share one path drawn in proportion to
+     * |p| from counter (group, t, 0x20000000); selection q draws step i
+     * uniformly on it and its partner j as an update does; round k pairs
+     * lane l's (i, e_i) with lane (l + o_k) mod 32's (j, e_j), o_0 = 0,
+     * o_k = 1 + mulhi32(word k - 1 of blocks 1, 2 of the group counter, 31).
+     * Step reduction factor SRF (1..2^20, default 1): an iteration has
+     * ceil(updates_per_step x S / SRF) selections (or updates, with DRF 1).
+     * Both need PGSGD_OPT_PIPELINE = 0. */
+    PGSGD_OPT_DRF = 17,
+    PGSGD_OPT_SRF = 18
 } pgsgd_option;
 
 /* Device-resident graph: node records, packed step records, path table. */
@@ -236,6 +253,19 @@ int pgsgd_stress(pgsgd_graph *g, uint32_t samples_per_step, uint64_t seed,
 int pgsgd_debug_sample(pgsgd_graph *g, uint32_t t, uint32_t iter_max, double theta,
                        uint64_t seed, uint64_t u_begin, uint64_t count,
                        pgsgd_sample *out, void *cuda_stream);
+
+/*
+ * With data reuse on (PGSGD_OPT_DRF > 1): the DRF pairs of every selection q
+ * in [q_begin, q_begin + count) of iteration t, out[count][DRF] (host),
+ * round k in column k: g = the global step of i, i and path as drawn by
+ * selection q, j / e_j / cooling those of the round's partner lane; skip = 1
+ * when the path has < 2 steps or the partner selection is past the
+ * iteration's ceil(updates_per_step x S / SRF) selections. Honors
+ * PGSGD_OPT_WARP_MERGE. pgsgd_debug_sample also honors it. Synchronous.
+ */
+int pgsgd_debug_sample_reuse(pgsgd_graph *g, uint32_t t, uint32_t iter_max, double theta,
+                             uint64_t seed, uint64_t q_begin, uint64_t count,
+                             pgsgd_sample *out, void *cuda_stream);
 
 /*
  * Jacobi sweep: for every update u in [u_begin, u_begin + count) of

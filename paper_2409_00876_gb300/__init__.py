@@ -177,6 +177,15 @@ class Graph:
                                              stream or _current_stream()))
         return out
 
+    def debug_sample_reuse(self, t, iter_max, theta, seed, q_begin, count, stream=None):
+        """With data reuse on: [count, drf] pair records of selections q_begin.. ."""
+        drf = self.get_option("drf")
+        out = np.zeros(count * drf, dtype=SAMPLE_DTYPE)
+        N.check(self._lib.pgsgd_debug_sample_reuse(self._h, t, iter_max, float(theta), int(seed), int(q_begin),
+                                                   int(count), out.ctypes.data_as(C.c_void_p),
+                                                   stream or _current_stream()))
+        return out.reshape(count, drf)
+
     def debug_sweep(self, t, iter_max, eta, theta, seed, u_begin, count, stream=None):
         out = np.zeros((count, 4), dtype=np.float32)
         N.check(self._lib.pgsgd_debug_sweep(self._h, t, iter_max, float(eta), float(theta),

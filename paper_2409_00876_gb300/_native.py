@@ -18,7 +18,8 @@ PGSGD_OK, PGSGD_EINVAL, PGSGD_ERANGE, PGSGD_ENOMEM, PGSGD_ECUDA, PGSGD_ETIMEOUT,
 
 OPT = dict(coord_mode=1, updates_per_step=2, block=3, blocks_per_sm=4, updates_per_thread=5,
            atomic_updates=6, rebase=7, timing=8, max_concurrent=9,
-           min_blocks=10, l2_fetch=11, store_mode=12, l2_hints=13, prefetch64=14, pipeline=15)
+           min_blocks=10, l2_fetch=11, store_mode=12, l2_hints=13, prefetch64=14, pipeline=15,
+           warp_merge=16, drf=17, srf=18)
 
 
 BOPT = dict(mode=1, cuda_graph=2, block=3, updates_per_thread=4, chunk=5, max_concurrent=6,
@@ -59,6 +60,7 @@ _SIGS = {
     "pgsgd_layout": ([P, u32, P, dbl, dbl, dbl, u64, u32, u32, P], i32),
     "pgsgd_stress": ([P, u32, u64, P, P, P], i32),
     "pgsgd_debug_sample": ([P, u32, u32, dbl, u64, u64, u64, P, P], i32),
+    "pgsgd_debug_sample_reuse": ([P, u32, u32, dbl, u64, u64, u64, P, P], i32),
     "pgsgd_debug_sweep": ([P, u32, u32, dbl, dbl, u64, u64, u64, P, P], i32),
     "pgsgd_timing_read": ([P, P, P, P, i32], i32),
     "pgsgd_stress_noalloc": ([P, u32, P, u32, P, P, P, P, u32, u64, P, P], i32),

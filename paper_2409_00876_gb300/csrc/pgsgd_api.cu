@@ -149,6 +149,7 @@ SamplerArgs sampler_args(const pgsgd_graph* g, uint32_t T, uint32_t t, float the
     a.t = t;
     a.key0 = (uint32_t)seed;
     a.key1 = (uint32_t)(seed >> 32);
+    a.wm = g->warp_merge ? 1u : 0u;
     a.zc.theta = theta;
     a.zc.omt = a.zc.A = a.zc.s = 0.0f;
     return a;
@@ -425,6 +426,17 @@ int pgsgd_set_option(pgsgd_graph* g, int option, int64_t v) {
         case PGSGD_OPT_PIPELINE:
             g->pipeline = v ? 1 : 0;
             return PGSGD_OK;
+        case PGSGD_OPT_WARP_MERGE:
+            g->warp_merge = v ? 1 : 0;
+            return PGSGD_OK;
+        case PGSGD_OPT_DRF:
+            if (v != 1 && v != 2 && v != 4 && v != 8) return fail(PGSGD_EINVAL, "data reuse factor must be 1, 2, 4 or 8");
+            g->drf = (int)v;
+            return PGSGD_OK;
+        case PGSGD_OPT_SRF:
+            if (v < 1 || v > (1 << 20)) return fail(PGSGD_EINVAL, "step reduction factor must be in [1, 2^20]");
+            g->srf = (int)v;
+            return PGSGD_OK;
         case PGSGD_OPT_L2_FETCH:
             if (v != 0 && v != 32 && v != 64 && v != 128)
                 return fail(PGSGD_EINVAL, "L2 fetch granularity must be 0, 32, 64 or 128");
@@ -453,6 +465,9 @@ int pgsgd_get_option(const pgsgd_graph* g, int option, int64_t* v) {
         case PGSGD_OPT_L2_HINTS: *v = g->l2_hints; return PGSGD_OK;
         case PGSGD_OPT_PREFETCH64: *v = g->pf64; return PGSGD_OK;
         case PGSGD_OPT_PIPELINE: *v = g->pipeline; return PGSGD_OK;
+        case PGSGD_OPT_WARP_MERGE: *v = g->warp_merge; return PGSGD_OK;
+        case PGSGD_OPT_DRF: *v = g->drf; return PGSGD_OK;
+        case PGSGD_OPT_SRF: *v = g->srf; return PGSGD_OK;
         default: return fail(PGSGD_EINVAL, "unknown option %d", option);
     }
 }
@@ -539,14 +554,20 @@ int pgsgd_layout(pgsgd_graph* g, uint32_t iter_max, const double* eta, double et
     const float th = (float)theta;
     rc = ensure_zipf(g, th, st);
     if (rc) return rc;
-    const uint64_t N = (uint64_t)g->updates_per_step * g->n_steps;
+    if (g->pipeline && (g->warp_merge || g->drf > 1))
+        return fail(PGSGD_EINVAL, "warp merging and data reuse run the plain update loop: set pipeline 0");
+    // updates per iteration (Algorithm 1, line 1) cut by the step reduction
+    // factor; with data reuse the kernel counts selections of drf updates
+    const uint64_t N_full = (uint64_t)g->updates_per_step * g->n_steps;
+    const uint64_t N = (N_full + (uint64_t)g->srf - 1) / (uint64_t)g->srf;
+    const uint64_t updates_per_launch = N * (uint64_t)g->drf;
     // grid: a multiple of the SM count, capped by the concurrency limit
     const int per_sm = g->blocks_per_sm;
     int grid = g->sm_count * per_sm;
     int64_t cap = g->max_concurrent;
     if (cap == -1) cap = std::max<int64_t>(2048, (int64_t)g->n_nodes / 2);
     if (cap > 0) {
-        const int64_t per_block = (int64_t)g->block * g->upt;
+        const int64_t per_block = (int64_t)g->block * (g->drf > 1 ? 1 : g->upt);
         const int64_t gmax = std::max<int64_t>(1, cap / per_block);
         if (gmax < grid) grid = (int)gmax;
     }
@@ -562,6 +583,8 @@ int pgsgd_layout(pgsgd_graph* g, uint32_t iter_max, const double* eta, double et
     L.l2_hints = g->l2_hints != 0;
     L.pf64 = g->pf64;
     L.pipeline = g->pipeline != 0;
+    L.wm = g->warp_merge != 0;
+    L.drf = g->drf;
     L.atomic = g->atomic != 0;
     if (g->l2_fetch) CK(cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, g->l2_fetch), "L2 fetch limit");
     for (uint32_t t = iter_begin; t < iter_end; ++t) {
@@ -578,7 +601,7 @@ int pgsgd_layout(pgsgd_graph* g, uint32_t iter_max, const double* eta, double et
             CK(cudaEventRecord(e1, st), "timing event");
             g->ev_pending.emplace_back(e0, e1);
             g->timing_launches += 1;
-            g->timing_updates += N;
+            g->timing_updates += updates_per_launch;
         }
         if (g->rebase && g->coord_mode == 0) {
             CK(launch_rebase(g->d_nodes, g->d_anchor, g->n_nodes, g->d_changed, g->sm_count, st), "rebase");
@@ -689,6 +712,29 @@ int pgsgd_debug_sample(pgsgd_graph* g, uint32_t t, uint32_t iter_max, double the
                            g->sm_count, st), "debug sample");
     CK(cudaMemcpyAsync(out, g->d_debug, count * sizeof(pgsgd_sample), cudaMemcpyDeviceToHost, st),
        "debug readback");
+    CK(cudaStreamSynchronize(st), "debug sync");
+    return PGSGD_OK;
+}
+
+int pgsgd_debug_sample_reuse(pgsgd_graph* g, uint32_t t, uint32_t iter_max, double theta, uint64_t seed,
+                             uint64_t q_begin, uint64_t count, pgsgd_sample* out, void* cuda_stream) {
+    if (!g || (!out && count)) return fail(PGSGD_EINVAL, "NULL argument");
+    if (iter_max == 0 || t >= iter_max) return fail(PGSGD_EINVAL, "need t < iter_max");
+    if (g->drf < 2) return fail(PGSGD_EINVAL, "data reuse is off (PGSGD_OPT_DRF = 1)");
+    int rc = check_theta(theta);
+    if (rc) return rc;
+    if (count == 0) return PGSGD_OK;
+    cudaStream_t st = S(cuda_stream);
+    rc = ensure_zipf(g, (float)theta, st);
+    if (rc) return rc;
+    const uint64_t n = count * (uint64_t)g->drf;
+    rc = ensure_debug(g, n * sizeof(pgsgd_sample));
+    if (rc) return rc;
+    const uint64_t n_sel = ((uint64_t)g->updates_per_step * g->n_steps + g->srf - 1) / (uint64_t)g->srf;
+    const SamplerArgs a = sampler_args(g, iter_max, t, (float)theta, seed);
+    CK(launch_debug_sample_reuse(a, (uint32_t)g->drf, n_sel, q_begin, count, g->d_debug, g->sm_count, st),
+       "debug sample kernel");
+    CK(cudaMemcpyAsync(out, g->d_debug, n * sizeof(pgsgd_sample), cudaMemcpyDeviceToHost, st), "debug readback");
     CK(cudaStreamSynchronize(st), "debug sync");
     return PGSGD_OK;
 }

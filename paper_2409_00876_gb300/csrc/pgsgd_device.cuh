@@ -285,6 +285,7 @@ struct SamplerArgs {
     uint32_t T;                // iterations in the schedule
     uint32_t t;                // this iteration
     uint32_t key0, key1;       // Philox key = seed
+    uint32_t wm;               // warp merging: cooling coin per group of 32 updates (debug kernels)
     ZipfConsts zc;
 };
 
@@ -356,27 +357,49 @@ __device__ __forceinline__ uint64_t draw_partner(const ZipfConsts& zc, const flo
     return (n - 1 - i > i) ? n - 1 : 0;
 }
 
-// Draw the pair of update u in iteration t (Algorithm 1, lines 5-11). One
-// Philox block serves the whole draw: w0, w1 pick the step, bits 0-3 of w2
-// are the coins, w3 feeds the first power-law trial or, with the upper 28
-// bits of w2, the uniform partner. Later blocks are drawn only after a
-// power-law trial rejects (about 1 update in 1000).
-__device__ __forceinline__ Pair draw_pair(const SamplerArgs& a, const PathTable& pt, uint64_t u) {
+__device__ __forceinline__ uint4 pair_block(const SamplerArgs& a, uint64_t u) {
+    return philox4x32_10(make_uint4((uint32_t)u, (uint32_t)(u >> 32), a.t, 0u), a.key0, a.key1);
+}
+
+// The pair of update u from its block-0 words w, with cooling coin `coin`.
+__device__ __forceinline__ Pair pair_from_block(const SamplerArgs& a, const PathTable& pt, uint64_t u, uint4 w,
+                                                uint32_t coin) {
     Pair r;
     const uint32_t c0 = (uint32_t)u, c1 = (uint32_t)(u >> 32);
-    const uint4 w = philox4x32_10(make_uint4(c0, c1, a.t, 0u), a.key0, a.key1);
     r.g = mulhi64((uint64_t)w.x | ((uint64_t)w.y << 32), a.n_steps);
     r.path = find_path_guided(pt, r.g);
     r.base = pt.off[r.path];
     const uint64_t n = pt.off[r.path + 1] - r.base;
     r.i = r.g - r.base;
     r.w2 = w.z;
-    r.cooling = (2ull * a.t >= a.T) || (w.z & 1u);
+    r.cooling = (2ull * a.t >= a.T) || coin;
     r.short_path = n < 2;
     r.j = r.short_path ? r.i
                        : draw_partner(a.zc, pt.T, pt.B[r.path], n, r.i, r.cooling, w.z, w.w, c0, c1, a.t, a.key0,
                                       a.key1);
     return r;
+}
+
+// Draw the pair of update u in iteration t (Algorithm 1, lines 5-11). One
+// Philox block serves the whole draw: w0, w1 pick the step, bits 0-3 of w2
+// are the coins, w3 feeds the first power-law trial or, with the upper 28
+// bits of w2, the uniform partner. Later blocks are drawn only after a
+// power-law trial rejects (about 1 update in 1000).
+__device__ __forceinline__ Pair draw_pair(const SamplerArgs& a, const PathTable& pt, uint64_t u) {
+    const uint4 w = pair_block(a, u);
+    return pair_from_block(a, pt, u, w, w.z & 1u);
+}
+
+// Warp merging (Section V-B3): the cooling coin of update u is bit 0 of w2
+// of update 32 floor(u / 32), computed here from scratch (no warp needed).
+__device__ __forceinline__ uint32_t group_coin(const SamplerArgs& a, uint64_t u) {
+    return pair_block(a, u & ~31ull).z & 1u;
+}
+
+// draw_pair, or with a.wm its warp-merged form (debug and checking kernels).
+__device__ __forceinline__ Pair draw_pair_any(const SamplerArgs& a, const PathTable& pt, uint64_t u) {
+    const uint4 w = pair_block(a, u);
+    return pair_from_block(a, pt, u, w, a.wm ? group_coin(a, u) : (w.z & 1u));
 }
 
 // ---------------------------------------------------------------- shared kernel helpers
@@ -410,13 +433,12 @@ struct Move {
 
 // The update of Zheng et al. that Algorithm 1, line 15 applies (Fig. 3):
 // w = d^-2, mu = min(eta w, 1), r = mu (|v_i - v_j| - d) / (2 |v_i - v_j|),
-// v_i -= r (v_i - v_j), v_j += r (v_i - v_j). FP32; x anchors differenced in
-// integers so chromosome-scale coordinates keep their resolution.
-__device__ __forceinline__ Move pair_move(const NodeRec& a, int32_t axa, uint32_t ea, const NodeRec& b,
-                                          int32_t axb, uint32_t eb, int64_t d, float eta) {
+// v_i -= r (v_i - v_j), v_j += r (v_i - v_j), for the points (xa, ya) and
+// (xb, yb). FP32; x anchors differenced in integers so chromosome-scale
+// coordinates keep their resolution.
+__device__ __forceinline__ Move point_move(float xa, float ya, int32_t axa, float xb, float yb, int32_t axb,
+                                           int64_t d, float eta) {
     Move m;
-    const float xa = ea ? a.ex : a.sx, ya = ea ? a.ey : a.sy;
-    const float xb = eb ? b.ex : b.sx, yb = eb ? b.ey : b.sy;
     const float dx = __ll2float_rn((int64_t)axa - (int64_t)axb) + (xa - xb);
     const float dy = ya - yb;
     const float mag = sqrtf(dx * dx + dy * dy);
@@ -428,6 +450,12 @@ __device__ __forceinline__ Move pair_move(const NodeRec& a, int32_t axa, uint32_
     const float rx = r * dx, ry = r * dy;
     m.dxi = -rx; m.dyi = -ry; m.dxj = rx; m.dyj = ry;
     return m;
+}
+
+// The same for endpoint ea of node a and endpoint eb of node b.
+__device__ __forceinline__ Move pair_move(const NodeRec& a, int32_t axa, uint32_t ea, const NodeRec& b,
+                                          int32_t axb, uint32_t eb, int64_t d, float eta) {
+    return point_move(ea ? a.ex : a.sx, ea ? a.ey : a.sy, axa, eb ? b.ex : b.sx, eb ? b.ey : b.sy, axb, d, eta);
 }
 
 
@@ -550,6 +578,179 @@ __device__ __forceinline__ void update_range_pipelined(const SamplerArgs& a, con
         draw_trip<UPT>(a, pt, base + trip, stride, u_end, nxt);
         finish_trip<UPT>(nodes, cur, si, sj, o, pol_keep);
         cur = nxt;
+    }
+}
+
+// ---------------------------------------------------------------- warp merging and data reuse
+
+// Warp merging: a warp's lanes hold 32 consecutive update indices starting
+// at a multiple of 32 (lane l holds 32 G + l), so lane 0's coin is the
+// group's and the warp shares it by shuffle. All 32 lanes must call this.
+template <int UPT>
+__device__ __forceinline__ void draw_trip_wm(const SamplerArgs& a, const PathTable& pt, uint64_t u0, uint64_t stride,
+                                             uint64_t u_end, TripDraws<UPT>& d) {
+#pragma unroll
+    for (int k = 0; k < UPT; ++k) {
+        const uint64_t u = u0 + (uint64_t)k * stride;
+        const uint4 w = pair_block(a, u);
+        const uint32_t coin = __shfl_sync(0xffffffffu, w.z & 1u, 0);
+        d.act[k] = u < u_end;
+        if (d.act[k]) {
+            const Pair pr = pair_from_block(a, pt, u, w, coin);
+            d.act[k] = !pr.short_path;
+            d.gi[k] = pr.base + pr.i;
+            d.gj[k] = pr.base + pr.j;
+            d.w2[k] = pr.w2;
+        }
+    }
+}
+
+template <int UPT>
+__device__ __forceinline__ void update_trip_wm(const SamplerArgs& a, const PathTable& pt, NodeRec* __restrict__ nodes,
+                                               uint64_t u0, uint64_t stride, uint64_t u_end, const UpdateOpts& o,
+                                               uint64_t pol_stream, uint64_t pol_keep) {
+    TripDraws<UPT> d;
+    draw_trip_wm<UPT>(a, pt, u0, stride, u_end, d);
+    StepRec si[UPT], sj[UPT];
+    load_trip_steps<UPT>(a.steps, d, si, sj, pol_stream, o.pf64);
+    finish_trip<UPT>(nodes, d, si, sj, o, pol_keep);
+}
+
+// Data reuse (Section VII-D). Group grp = q / 32 of selections shares one
+// path, drawn in proportion to |p| from block 0 of counter (grp, t,
+// 0x20000000); blocks 1 and 2 give the round offsets o_k = 1 + mulhi32(word,
+// 31), word k - 1 in order.
+__device__ __forceinline__ uint4 group_block(const SamplerArgs& a, uint64_t grp, uint32_t b) {
+    return philox4x32_10(make_uint4((uint32_t)grp, (uint32_t)(grp >> 32), a.t, 0x20000000u | b), a.key0, a.key1);
+}
+
+__device__ __forceinline__ uint32_t group_path(const SamplerArgs& a, const PathTable& pt, uint64_t grp) {
+    const uint4 w = group_block(a, grp, 0);
+    return find_path_guided(pt, mulhi64((uint64_t)w.x | ((uint64_t)w.y << 32), a.n_steps));
+}
+
+__device__ __forceinline__ uint32_t word_of(uint4 w, int k) {
+    return k == 0 ? w.x : k == 1 ? w.y : k == 2 ? w.z : w.w;
+}
+
+// Offset of round k >= 1 (one block per call: for checking kernels).
+__device__ __forceinline__ uint32_t reuse_offset(const SamplerArgs& a, uint64_t grp, uint32_t k) {
+    if (k == 0) return 0;
+    const uint32_t idx = k - 1;
+    return 1u + __umulhi(word_of(group_block(a, grp, 1 + idx / 4), idx % 4), 31u);
+}
+
+// All R offsets of a group (o[0] = 0), one block per four rounds.
+template <int R>
+__device__ __forceinline__ void reuse_offsets(const SamplerArgs& a, uint64_t grp, uint32_t (&o)[R]) {
+    o[0] = 0;
+    uint4 w = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+    for (int k = 1; k < R; ++k) {
+        const int idx = k - 1;
+        if (idx % 4 == 0) w = group_block(a, grp, 1 + idx / 4);
+        o[k] = 1u + __umulhi(word_of(w, idx % 4), 31u);
+    }
+}
+
+struct Selection {
+    uint64_t i, j;     // steps within the group's path
+    uint32_t w2;       // coin word: endpoint bits 2 and 3
+    uint32_t cooling;
+    bool valid;        // the path has at least two steps
+};
+
+// Selection q on path p from its block-0 words w: step i uniform on the path,
+// partner j as an update draws it.
+__device__ __forceinline__ Selection draw_selection(const SamplerArgs& a, const PathTable& pt, uint64_t q, uint32_t p,
+                                                    uint4 w, uint32_t coin) {
+    Selection s;
+    const uint64_t off = pt.off[p], n = pt.off[p + 1] - off;
+    s.w2 = w.z;
+    s.cooling = (2ull * a.t >= a.T) || coin;
+    s.valid = n >= 2;
+    s.i = s.valid ? mulhi64((uint64_t)w.x | ((uint64_t)w.y << 32), n) : 0;
+    s.j = s.valid ? draw_partner(a.zc, pt.T, pt.B[p], n, s.i, s.cooling, w.z, w.w, (uint32_t)q, (uint32_t)(q >> 32),
+                                 a.t, a.key0, a.key1)
+                  : 0;
+    return s;
+}
+
+// Selections q_first + m * stride below n_sel, one per thread per trip, each
+// performing R updates: round k pairs this lane's (i, e_i) with lane
+// (lane + o_k)'s (j, e_j). Points live in registers across the rounds; the
+// lane holding a j-point receives its move by shuffle. Each selection writes
+// its two points once, after the last round. Every lane of a warp runs the
+// same trips (the loop bound is the warp's first selection), so the shuffles
+// always see 32 lanes; stride and q_first - lane are multiples of 32.
+template <int R>
+__device__ __forceinline__ void reuse_range(const SamplerArgs& a, const PathTable& pt, NodeRec* __restrict__ nodes,
+                                            uint64_t q_first, uint64_t stride, uint64_t n_sel, float eta, bool wm,
+                                            int pf64, uint64_t pol_stream, uint64_t pol_keep) {
+    const uint32_t lane = threadIdx.x & 31u;
+    for (uint64_t q = q_first; q - lane < n_sel; q += stride) {
+        const uint64_t grp = q >> 5;
+        const uint32_t p = group_path(a, pt, grp);
+        uint32_t o[R];
+        reuse_offsets<R>(a, grp, o);
+        const uint4 w = pair_block(a, q);
+        const uint32_t coin = wm ? __shfl_sync(0xffffffffu, w.z & 1u, 0) : (w.z & 1u);
+        const Selection s = draw_selection(a, pt, q, p, w, coin);
+        const bool sel = s.valid && q < n_sel;
+        const uint64_t base = pt.off[p];
+        const uint32_t ei = (s.w2 >> 2) & 1u, ej = (s.w2 >> 3) & 1u;
+        uint32_t ni = 0, nj = 0;
+        float xi = 0.f, yi = 0.f, xj = 0.f, yj = 0.f;
+        int32_t axi = 0, axj = 0;
+        long long pi = 0, pj = 0;
+        if (sel) {
+            const StepRec si = load_step(a.steps + base + s.i, pol_stream, pf64 & 1);
+            const StepRec sj = load_step(a.steps + base + s.j, pol_stream, pf64 & 1);
+            ni = step_node(si);
+            nj = step_node(sj);
+            const NodeRec na = load_node(nodes + ni, pol_keep, pf64 & 2);
+            const NodeRec nb = load_node(nodes + nj, pol_keep, pf64 & 2);
+            xi = ei ? na.ex : na.sx;
+            yi = ei ? na.ey : na.sy;
+            xj = ej ? nb.ex : nb.sx;
+            yj = ej ? nb.ey : nb.sy;
+            axi = si.ax;
+            axj = sj.ax;
+            pi = endpoint_pos(si, ei);
+            pj = endpoint_pos(sj, ej);
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const uint32_t m = (lane + o[k]) & 31u;
+            const float xm = __shfl_sync(0xffffffffu, xj, m), ym = __shfl_sync(0xffffffffu, yj, m);
+            const int32_t axm = __shfl_sync(0xffffffffu, axj, m);
+            const long long pm = __shfl_sync(0xffffffffu, pj, m);
+            const int selm = __shfl_sync(0xffffffffu, (int)sel, m);
+            float nxm = xm, nym = ym;
+            if (sel && selm) {
+                const long long d = pi > pm ? pi - pm : pm - pi;
+                if (d != 0) {
+                    const Move mv = point_move(xi, yi, axi, xm, ym, axm, (int64_t)d, eta);
+                    if (mv.moved) {
+                        xi += mv.dxi;
+                        yi += mv.dyi;
+                        nxm = xm + mv.dxj;
+                        nym = ym + mv.dyj;
+                    }
+                }
+            }
+            // the move of lane m's j-point goes back to lane m
+            const uint32_t src = (lane - o[k]) & 31u;
+            const float rx = __shfl_sync(0xffffffffu, nxm, src), ry = __shfl_sync(0xffffffffu, nym, src);
+            if (sel) {
+                xj = rx;
+                yj = ry;
+            }
+        }
+        if (sel) {
+            exchange_point(&nodes[ni].sx + 2 * ei, xi, yi, pol_keep);
+            exchange_point(&nodes[nj].sx + 2 * ej, xj, yj, pol_keep);
+        }
     }
 }
 }  // namespace pgsgd

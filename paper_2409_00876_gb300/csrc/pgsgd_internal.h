@@ -40,6 +40,8 @@ struct UpdateLaunch {
     int pf64;            // 64-byte L2 prefetch hint: bit 0 step loads, bit 1 node loads
     bool atomic;
     bool pipeline;       // software-pipelined update loop
+    bool wm;             // warp merging: one cooling coin per group of 32 updates
+    int drf;             // data reuse factor (> 1: n_updates counts selections of drf updates)
 };
 
 struct StressLaunch {
@@ -82,6 +84,8 @@ cudaError_t launch_refresh_anchors(StepRec* steps, const int32_t* anchor, uint64
 cudaError_t launch_zipf_setup(const uint64_t* path_off, uint32_t n_paths, float theta, float* zipf_B,
                               float* zipf_T, cudaStream_t st);
 cudaError_t launch_update(const UpdateLaunch& L, cudaStream_t st);
+cudaError_t launch_debug_sample_reuse(const SamplerArgs& s, uint32_t R, uint64_t n_sel, uint64_t q_begin,
+                                     uint64_t count, void* out, int sm_count, cudaStream_t st);
 cudaError_t launch_debug_sample(const SamplerArgs& s, uint64_t u_begin, uint64_t count, void* out,
                                 int sm_count, cudaStream_t st);
 cudaError_t launch_debug_sweep(const SamplerArgs& s, uint64_t u_begin, uint64_t count, const NodeRec* nodes,
@@ -152,6 +156,9 @@ struct pgsgd_graph {
     int l2_hints = 1;
     int pf64 = 7;
     int pipeline = 0;
+    int warp_merge = 0;
+    int drf = 1;          // data reuse factor
+    int srf = 1;          // step reduction factor
 
     // timing
     std::vector<cudaEvent_t> ev_free;

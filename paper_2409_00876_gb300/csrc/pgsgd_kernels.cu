@@ -202,6 +202,44 @@ __global__ void __launch_bounds__(256, MINB) update_kernel(UpdateLaunch L) {
     }
 }
 
+// Warp merging (Section V-B3): the update kernel with one cooling coin per
+// group of 32 updates, shared by shuffle. The loop bound is the warp's first
+// update so all 32 lanes run every trip (u_begin is a multiple of 32).
+template <int UPT>
+__global__ void __launch_bounds__(256, 1) update_kernel_wm(UpdateLaunch L) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ ZipfConsts zc;
+    const PathTable pt = stage_paths(L.s, smem, zc);
+    SamplerArgs a = L.s;
+    a.zc = zc;
+    const uint64_t pol_stream = L.l2_hints ? policy_evict_first() : 0;
+    const uint64_t pol_keep = L.l2_hints ? policy_evict_last() : 0;
+    const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t gtid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint64_t lane = threadIdx.x & 31u;
+    const UpdateOpts o{L.eta, L.store_mode, L.pf64, L.atomic};
+    const uint64_t u_end = L.u_begin + L.n_updates;
+    for (uint64_t base = L.u_begin + gtid; base - lane < u_end; base += nthr * UPT)
+        update_trip_wm<UPT>(a, pt, L.nodes, base, nthr, u_end, o, pol_stream, pol_keep);
+}
+
+// Warp-level data reuse (Section VII-D): n_updates = selections, each doing
+// R updates (reuse_range).
+template <int R>
+__global__ void __launch_bounds__(256, 1) update_reuse_kernel(UpdateLaunch L) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ ZipfConsts zc;
+    const PathTable pt = stage_paths(L.s, smem, zc);
+    SamplerArgs a = L.s;
+    a.zc = zc;
+    const uint64_t pol_stream = L.l2_hints ? policy_evict_first() : 0;
+    const uint64_t pol_keep = L.l2_hints ? policy_evict_last() : 0;
+    const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t gtid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    reuse_range<R>(a, pt, L.nodes, L.u_begin + gtid, nthr, L.u_begin + L.n_updates, L.eta, L.wm, L.pf64, pol_stream,
+                   pol_keep);
+}
+
 // ---------------------------------------------------------------- debug kernels
 
 __global__ void debug_sample_kernel(SamplerArgs a0, uint64_t u_begin, uint64_t count, pgsgd_sample* out) {
@@ -212,7 +250,7 @@ __global__ void debug_sample_kernel(SamplerArgs a0, uint64_t u_begin, uint64_t c
     a.zc = zc;
     for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < count;
          q += (uint64_t)gridDim.x * blockDim.x) {
-        const Pair pr = draw_pair(a, pt, u_begin + q);
+        const Pair pr = draw_pair_any(a, pt, u_begin + q);
         pgsgd_sample r;
         r.g = pr.g; r.i = pr.i; r.j = pr.j; r.path = pr.path;
         r.cooling = (uint8_t)pr.cooling;
@@ -240,7 +278,7 @@ __global__ void debug_sweep_kernel(SamplerArgs a0, uint64_t u_begin, uint64_t co
     a.zc = zc;
     for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < count;
          q += (uint64_t)gridDim.x * blockDim.x) {
-        const Pair pr = draw_pair(a, pt, u_begin + q);
+        const Pair pr = draw_pair_any(a, pt, u_begin + q);
         float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
         if (!pr.short_path) {
             const StepRec si = a.steps[pr.base + pr.i], sj = a.steps[pr.base + pr.j];
@@ -254,6 +292,48 @@ __global__ void debug_sweep_kernel(SamplerArgs a0, uint64_t u_begin, uint64_t co
             }
         }
         out[q] = o;
+    }
+}
+
+// The R pairs of every selection q in [q_begin, q_begin + count) under data
+// reuse, computed from scratch (no shuffles): out[(q - q_begin) R + k].
+__global__ void debug_sample_reuse_kernel(SamplerArgs a0, uint32_t R, uint64_t n_sel, uint64_t q_begin,
+                                          uint64_t count, pgsgd_sample* out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ ZipfConsts zc;
+    const PathTable pt = stage_paths(a0, smem, zc);
+    SamplerArgs a = a0;
+    a.zc = zc;
+    for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < count * R;
+         c += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t q = q_begin + c / R;
+        const uint32_t k = (uint32_t)(c % R);
+        const uint64_t grp = q >> 5;
+        const uint32_t p = group_path(a, pt, grp);
+        const uint64_t qm = (grp << 5) | (((uint32_t)q + reuse_offset(a, grp, k)) & 31u);
+        const uint4 wq = pair_block(a, q), wm = pair_block(a, qm);
+        const Selection mine = draw_selection(a, pt, q, p, wq, a.wm ? group_coin(a, q) : (wq.z & 1u));
+        const Selection other = draw_selection(a, pt, qm, p, wm, a.wm ? group_coin(a, qm) : (wm.z & 1u));
+        const uint64_t base = pt.off[p];
+        pgsgd_sample r;
+        r.g = base + mine.i;
+        r.i = mine.i;
+        r.j = other.j;
+        r.path = p;
+        r.cooling = (uint8_t)other.cooling;
+        r.e_i = (mine.w2 >> 2) & 1u;
+        r.e_j = (other.w2 >> 3) & 1u;
+        r.d_ref = 0;
+        r.skip = 0;
+        if (!(mine.valid && other.valid && q < n_sel && qm < n_sel)) {
+            r.skip = 1;
+        } else {
+            const StepRec si = a.steps[base + mine.i], sj = a.steps[base + other.j];
+            const int64_t pa = endpoint_pos(si, r.e_i), pb = endpoint_pos(sj, r.e_j);
+            r.d_ref = pa > pb ? pa - pb : pb - pa;
+            r.skip = r.d_ref == 0 ? 2 : 0;
+        }
+        out[c] = r;
     }
 }
 
@@ -480,8 +560,33 @@ static cudaError_t launch_update_t(const UpdateLaunch& L, cudaStream_t st) {
 
 // UPT = updates in flight per thread; MINB = resident 256-thread blocks per
 // SM the register allocation must allow (1 = unconstrained).
+template <class K>
+static cudaError_t launch_with_smem(K kernel, const UpdateLaunch& L, cudaStream_t st) {
+    const size_t smem = update_smem_bytes(L.s.n_paths, L.s.n_guide);
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kernel<<<L.grid, L.block, smem, st>>>(L);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_update(const UpdateLaunch& L, cudaStream_t st) {
     if (L.n_updates == 0) return cudaSuccess;
+    if (L.drf > 1) {
+        switch (L.drf) {
+            case 2: return launch_with_smem(update_reuse_kernel<2>, L, st);
+            case 4: return launch_with_smem(update_reuse_kernel<4>, L, st);
+            case 8: return launch_with_smem(update_reuse_kernel<8>, L, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    if (L.wm) {
+        switch (L.upt) {
+            case 1: return launch_with_smem(update_kernel_wm<1>, L, st);
+            case 2: return launch_with_smem(update_kernel_wm<2>, L, st);
+            case 4: return launch_with_smem(update_kernel_wm<4>, L, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     if (L.pipeline) {
         switch (L.upt * 10 + L.minb) {
             case 11: return launch_update_t<1, 1, true>(L, st);
@@ -504,6 +609,18 @@ cudaError_t launch_update(const UpdateLaunch& L, cudaStream_t st) {
         case 43: return launch_update_t<4, 3>(L, st);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_debug_sample_reuse(const SamplerArgs& s, uint32_t R, uint64_t n_sel, uint64_t q_begin,
+                                     uint64_t count, void* out, int sm_count, cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    const size_t smem = update_smem_bytes(s.n_paths, s.n_guide);
+    cudaError_t e = cudaFuncSetAttribute(debug_sample_reuse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    debug_sample_reuse_kernel<<<grid_for(count * R, 256, sm_count, 8), 256, smem, st>>>(
+        s, R, n_sel, q_begin, count, static_cast<pgsgd_sample*>(out));
+    return cudaGetLastError();
 }
 
 cudaError_t launch_debug_sample(const SamplerArgs& s, uint64_t u_begin, uint64_t count, void* out,
