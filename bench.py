@@ -51,7 +51,9 @@ WORKLOADS = {
     "batch256": "256 independent synthetic subgraphs, node counts log-uniform in [1,000, 200,000], "
                 "path counts uniform in [4, 90] (8.6e6 nodes, 4.0e8 steps in all); 30 iterations "
                 "x 10 x steps updates per graph, each graph with its own learning-rate schedule",
+    "batch_prof": "64 independent synthetic subgraphs drawn like batch256 (profiling case, ~1.5 GB)",
 }
+BATCH_WORKLOADS = ("batch256", "batch_prof")
 BATCH_METRIC = "PG-SGD updates/sec, batched layout of 256 subgraphs (one persistent or CUDA-graph launch " \
                "sequence) vs one launch per graph; per-graph stress"
 
@@ -172,12 +174,12 @@ class ClockSampler:
 
 def make_workload(config):
     from synth import BATCH_CONFIGS, batch_shapes, make_batch, make_graph
-    if config == "batch256":
+    if config in BATCH_CONFIGS:
         # the oracle's bounded sample runs on the batch's largest graph
-        cfg = BATCH_CONFIGS["batch256"]
+        cfg = BATCH_CONFIGS[config]
         shapes = batch_shapes(cfg["n_graphs"], cfg["nodes"], cfg["paths"], cfg["seed"])
         k = max(range(len(shapes)), key=lambda i: shapes[i][0] * shapes[i][1])
-        return make_batch("batch256", indices=[k])[0]
+        return make_batch(config, indices=[k])[0]
     if config == "prof":
         return make_graph("chrom", backbone=2_000_000, paths=30)
     return make_graph(config)
@@ -319,7 +321,8 @@ def run_gpu(args):
 
     forms = None
     if rank == 0 and not args.no_forms and args.config == "chrom":
-        forms = {"batched": batch_form(dev), "differentiable": dstress_form(dev)}
+        forms = {"data_reuse": reuse_form(G, xy0), "batched": batch_form(dev),
+                 "differentiable": dstress_form(dev)}
 
     if rank == 0:
         line = {
@@ -362,7 +365,7 @@ def _batch_timed(B, xy, seeds, iter_end=None):
     return ms, launches, updates
 
 
-def batch_form(dev, full=False, log=None):
+def batch_form(dev, full=False, log=None, name="batch256"):
     """The 256-subgraph batch: autotuned batched schedule against one launch
     per graph (and, with full, the other schedules and separate one-graph
     handles), every schedule from the same initial layouts and seeds."""
@@ -370,7 +373,7 @@ def batch_form(dev, full=False, log=None):
     import paper_2409_00876_gb300 as pg
     from paper_2409_00876_gb300.batch import Batch, autotune
     from synth import concat, make_batch
-    gs = make_batch("batch256")
+    gs = make_batch(name)
     arr = concat(gs)
     B = Batch.from_arrays(arr)
     xy = torch.from_numpy(arr.init_xy).to(dev)
@@ -387,7 +390,7 @@ def batch_form(dev, full=False, log=None):
 
     _batch_timed(B, xy, seeds)  # warm: the tuned shape's CUDA graph
     ms, launches, _ = _batch_timed(B, xy, seeds)
-    out = {"workload": WORKLOADS["batch256"], "n_graphs": len(gs), "updates": updates,
+    out = {"workload": WORKLOADS[name], "n_graphs": len(gs), "updates": updates,
            "tuned": {**tuned, "mode": {0: "launch per iteration (CUDA graph)", 1: "persistent", 2: "per graph"}[
                tuned["mode"]]}, "autotune_s": round(tune_s, 1),
            "autotune_trials_ms": {"/".join(map(str, k)): round(v, 2) for k, v in table.items()},
@@ -468,6 +471,36 @@ def dstress_form(dev, n_pairs=10_000_000, steps=200):
             "timing": "host wall clock around synchronous calls (forward includes its readback)"}
 
 
+def reuse_form(G, xy0, schemes=((1, 1, 1), (2, 2, 0), (4, 4, 0), (8, 8, 0))):
+    """Warp merging and warp-level data reuse (DRF, SRF) on the same graph:
+    one full layout per scheme from the same initial layout and seed, its
+    time and its sampled stress, beside the plain method's."""
+    G.set_option("timing", 1)
+    out = []
+    try:
+        for drf, srf, wm in ((1, 1, 0),) + tuple(schemes):
+            G.set_option("drf", drf)
+            G.set_option("srf", srf)
+            G.set_option("warp_merge", wm)
+            G.set_coords(xy0)
+            G.timing_read(reset=True)
+            G.layout(ITERS, theta=THETA, seed=SEED)
+            ms, _, upd = G.timing_read(reset=True)
+            st = G.stress(STRESS_PER_STEP, seed=STRESS_SEED)
+            out.append({"drf": drf, "srf": srf, "warp_merge": wm, "layout_ms": ms, "updates": upd,
+                        "updates_per_s": upd / (ms / 1e3), "stress": st["mean"], "stress_ci": [st["ci_lo"], st["ci_hi"]]})
+    finally:
+        G.set_option("drf", 1)
+        G.set_option("srf", 1)
+        G.set_option("warp_merge", 0)
+        G.set_option("timing", 0)
+    base = out[0]
+    for r in out:
+        r["speedup"] = base["layout_ms"] / r["layout_ms"]
+        r["stress_ratio"] = r["stress"] / base["stress"]
+    return out
+
+
 def run_batch(args):
     """--config batch256: one JSON line for the batched schedule."""
     import torch
@@ -479,7 +512,7 @@ def run_batch(args):
     from paper_2409_00876_gb300.batch import Batch, autotune
     from synth import concat, make_batch
     pg.load_library()
-    gs = make_batch("batch256")
+    gs = make_batch(args.config)
     arr = concat(gs)
     B = Batch.from_arrays(arr)
     xy = torch.from_numpy(arr.init_xy).to(dev)
@@ -518,7 +551,7 @@ def run_batch(args):
     peak, peak_kind = peaks()
     achieved = BYTES_PER_UPDATE * upd / (lay_ms / 1e3) / 1e9
     B.close()
-    comp = batch_form(dev, full=True) if rank == 0 else None
+    comp = batch_form(dev, full=True, name=args.config) if rank == 0 and not args.no_forms else None
     if rank == 0:
         m = np.array([r["mean"] for r in st])
         per_launch = {0: ITERS, 1: 1, 2: ITERS * len(gs)}[tuned["mode"]]
@@ -526,9 +559,9 @@ def run_batch(args):
             "metric": BATCH_METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOADS["batch256"], "name": "batch256", "n_steps": S,
+            "config": {"workload": WORKLOADS[args.config], "name": args.config, "n_steps": S,
                        "updates_per_step": updates_per_step, "tuned": tuned,
-                       "l2": "inputs larger than L2 (6.6 GB of step records), no flush",
+                       "l2": f"inputs larger than L2 ({16 * S / 1e9:.1f} GB of step records), no flush",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "stress": {"mean_over_graphs": float(m.mean()), "max": float(m.max())},
             "layout_only_updates_per_s": upd / (lay_ms / 1e3),
@@ -617,13 +650,14 @@ def main(argv=None):
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-budget", type=float, default=10.0)
     ap.add_argument("--no-forms", action="store_true",
-                    help="skip the batched and differentiable forms on the chromosome run")
+                    help="skip the data-reuse, batched and differentiable forms (chromosome run) or the "
+                         "schedule comparison (batch runs)")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "gb300" and not os.environ.get("PGSGD_BENCH_ALLOW_SHORT"):
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
-    if args.config == "batch256":
+    if args.config in BATCH_WORKLOADS:
         return run_batch(args)
     return run_gpu(args)
 

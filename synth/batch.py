@@ -18,6 +18,8 @@ from .pangenome import CONFIGS, Graph, make_graph
 BATCH_CONFIGS = {
     "batch256": dict(n_graphs=256, nodes=(1_000, 200_000), paths=(4, 90), seed=11, base="mid"),
     "batch_small": dict(n_graphs=12, nodes=(1_000, 12_000), paths=(4, 12), seed=5, base="mid"),
+    # the same distributions, a quarter of the graphs: a profiling case of ~1.5 GB
+    "batch_prof": dict(n_graphs=64, nodes=(1_000, 200_000), paths=(4, 90), seed=13, base="mid"),
 }
 
 
