@@ -39,15 +39,17 @@
  *     holds g; i = g - off[p]. This is "p with probability |p| / S, then i
  *     uniform in p". Paths with fewer than two steps give no update.
  *   - cooling = (2 t >= T) or (w2 & 1).
- *   - Power law: k follows Zipf(theta) on [1, n_p - 1], drawn by
- *     rejection-inversion (Hoermann and Derflinger, ACM TOMACS 6(3), 1996)
- *     evaluated in IEEE binary32 with the operation order fixed below (no
- *     fused multiply-add anywhere; a draw with k >= 256 is accepted without
- *     the rejection test), one 32-bit word per trial: w3, then the four words
- *     of block 1, block 2 and so on, at most 64 trials (then k = 1). Direction bit
- *     (w2 >> 1) & 1: 1 = forward (j = i + k), 0 = backward (j = i - k); if that
- *     leaves the path the other direction is used; if both leave it, j is the
- *     path end farther from i.
+ *   - Power law: j is drawn with probability proportional to |j - i|^-theta
+ *     over the other steps of the path. A trial draws k from Zipf(theta) on
+ *     [1, n_p - 1] by rejection-inversion (Hoermann and Derflinger, ACM
+ *     TOMACS 6(3), 1996) evaluated in IEEE binary32 with the operation order
+ *     fixed below (no fused multiply-add anywhere; a draw with k >= 256 is
+ *     accepted without the rejection test) from bits 8-31 of its 32-bit
+ *     word, and a direction from bit 4 of the word (1 = forward); it is
+ *     accepted when the Zipf test accepts and i +- k lies on the path. The
+ *     trial words are w3, then w2 & ~15, then the four words of block 1,
+ *     block 2 and so on, at most 64 trials (then j = i + 1, or i - 1 at the
+ *     path's last step).
  *   - Uniform: r = w3 << 32 | (w2 & ~15) (60 random bits: bits 0-3 of w2 are
  *     the coins); x = mulhi64(r, n_p - 1); j = x + (x >= i). Uniform over the
  *     other steps to within (n_p - 1) / 2^60 relative.
@@ -360,18 +362,42 @@ static int64_t endpoint_pos(const orc_graph *G, uint64_t step, int e)
 
 /* Partner step j of step i on path p (n >= 2 steps) from the words w of   */
 /* block 0 of counter (c0, c1, t) (Algorithm 1, lines 6-11).                */
+/* One power-law trial with word w: k ~ Zipf(theta) on [1, n - 1] from bits */
+/* 8-31 of w, direction from bit 4 (1 = forward); accepted when the Zipf    */
+/* test accepts and step i +- k lies on the path.                            */
+static int partner_trial(const zipf_t *z, uint64_t n, uint64_t i, uint32_t w, uint64_t *j)
+{
+    uint64_t k;
+    if (!zipf_trial(z, w, &k)) return 0;
+    if (w & 16u) {
+        if (i + k < n) { *j = i + k; return 1; }
+    } else if (i >= k) {
+        *j = i - k; return 1;
+    }
+    return 0;
+}
+
+/* Partner step j of step i on path p (n >= 2 steps) from the words w of   */
+/* block 0 of counter (c0, c1, t) (Algorithm 1, lines 6-11). Uniform: j =   */
+/* x + (x >= i), x = mulhi64(w3 << 32 | (w2 & ~15), n - 1). Power law (the   */
+/* paper names only "Powerlaw"; reading: P(j) proportional to |j - i|^-theta */
+/* over the path's other steps): trials with the words w3, w2 & ~15, then    */
+/* the words of blocks 1, 2, ... of the counter, 64 at most; after 64       */
+/* failed trials j = i + 1 (i - 1 at the last step).                         */
 static uint64_t partner_step(const sampler_t *S, uint32_t p, uint64_t n, uint64_t i, int cooling,
                              const uint32_t w[4], uint32_t c0, uint32_t c1, uint32_t t)
 {
     if (cooling) {
-        uint64_t k = zipf_draw(&S->zipf[p], w[3], S->seed, c0, c1, t);
-        int fwd = (w[2] >> 1) & 1u;
-        int can_fwd = i + k < n, can_bwd = i >= k;
-        if (fwd && can_fwd) return i + k;
-        if (!fwd && can_bwd) return i - k;
-        if (can_fwd) return i + k;
-        if (can_bwd) return i - k;
-        return (n - 1 - i > i) ? n - 1 : 0;
+        const zipf_t *z = &S->zipf[p];
+        uint64_t j;
+        if (partner_trial(z, n, i, w[3], &j)) return j;
+        if (partner_trial(z, n, i, w[2] & ~15u, &j)) return j;
+        for (int m = 2; m < 64; ++m) {
+            uint32_t x[4];
+            philox_block(S->seed, c0, c1, t, (uint32_t)(1 + (m - 2) / 4), x);
+            if (partner_trial(z, n, i, x[(m - 2) % 4], &j)) return j;
+        }
+        return i + 1 < n ? i + 1 : i - 1;
     }
     uint64_t x = mulhi64(((uint64_t)w[3] << 32) | (w[2] & ~15u), n - 1);
     return x + (x >= i);

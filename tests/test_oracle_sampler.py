@@ -154,12 +154,36 @@ def test_two_step_path_always_pairs_the_two_steps():
         assert np.all(s["i"] + s["j"] == 1)
 
 
-def test_fallback_takes_far_end_when_both_directions_leave_path():
-    # n = 3, i = 1: k = 2 fits neither way -> j is an end (0 or 2), never i
+def test_power_law_partner_is_proportional_to_distance_power_over_the_path():
+    # P(j | i) proportional to |j - i|^-theta over the path's other steps,
+    # near the ends as well: no mass piles up on the end steps
+    n = 60
+    g = _graph_with_paths([n])
+    s = O.sample(g, 30, 20, 0.99, 8, 0, 2_000_000)
+    i = s["i"].astype(np.int64)
+    j = s["j"].astype(np.int64)
+    assert np.all((j >= 0) & (j < n) & (j != i))
+    for i0 in (0, 1, 7, 30, 58, 59):
+        sel = i == i0
+        counts = np.bincount(j[sel], minlength=n).astype(np.float64)
+        others = np.arange(n) != i0
+        probs = np.abs(np.arange(n) - i0)[others].astype(np.float64) ** -0.99
+        ok, p = _chi2_ok(counts[others], probs)
+        assert ok, (i0, p)
+
+
+def test_power_law_partner_on_a_three_step_path():
+    # from the middle step only k = 1 fits: either neighbour, equally often
     g = _graph_with_paths([3])
     s = O.sample(g, 30, 25, 0.99, 6, 0, 50_000)
-    assert np.all(s["i"] != s["j"])
-    assert np.all(s["j"] < 3)
+    mid = s["i"] == 1
+    assert np.all(np.isin(s["j"][mid], [0, 2]))
+    assert abs((s["j"][mid] == 2).mean() - 0.5) < 5 * 0.5 / np.sqrt(mid.sum())
+    # from an end, the partner is the middle step (k = 1) or the other end (k = 2)
+    end = s["i"] == 0
+    w = np.array([1.0, 2.0 ** -0.99])
+    ok, p = _chi2_ok([np.sum(s["j"][end] == 1), np.sum(s["j"][end] == 2)], w)
+    assert ok, p
 
 
 def test_reference_distance_fig3_worked_pair():
