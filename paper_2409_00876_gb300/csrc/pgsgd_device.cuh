@@ -324,14 +324,34 @@ struct Pair {
     uint64_t i, j;     // step indices within the path
     uint64_t g;        // global step drawn
     uint32_t path;
-    uint32_t w2;       // coin word: bit0 cooling coin, bit1 direction, bits 2-3 endpoints
+    uint32_t w2;       // coin word: bit 0 cooling coin, bits 2-3 endpoints
     uint32_t cooling;  // 1 = power-law pair
     uint32_t short_path;  // 1 = path has < 2 steps: no update
 };
 
+// One power-law trial with word w: k ~ Zipf(theta) on [1, n - 1] from bits
+// 8-31 of w, direction from bit 4 (1 = forward); accepted when the Zipf test
+// accepts and step i +- k lies on the path.
+__device__ __forceinline__ bool partner_trial(const ZipfConsts& zc, const float* T, float B, uint64_t n, uint64_t i,
+                                              uint32_t w, uint64_t& j) {
+    uint64_t k = 1;
+    if (!zipf_trial(zc, T, B, n - 1, w, k)) return false;
+    if (w & 16u) {
+        if (i + k < n) { j = i + k; return true; }
+    } else if (i >= k) {
+        j = i - k;
+        return true;
+    }
+    return false;
+}
+
 // Partner step j of step i in a path of n >= 2 steps (Algorithm 1, lines
-// 6-11) from the coin word w2 and the word w3 of block 0 of the update's
-// counter (c0, c1, t); later blocks only after a power-law trial rejects.
+// 6-11) from the words w2, w3 of block 0 of the update's counter (c0, c1, t).
+// Uniform: j = x + (x >= i), x = mulhi64(w3 << 32 | (w2 & ~15), n - 1).
+// Power law: P(j) proportional to |j - i|^-theta over the path's other
+// steps: trials with the words w3, w2 & ~15, then blocks 1, 2, ... of the
+// counter (drawn only when needed), 64 at most, then j = i + 1 (i - 1 at the
+// last step).
 __device__ __forceinline__ uint64_t draw_partner(const ZipfConsts& zc, const float* T, float B, uint64_t n,
                                                  uint64_t i, bool cooling, uint32_t w2, uint32_t w3, uint32_t c0,
                                                  uint32_t c1, uint32_t t, uint32_t key0, uint32_t key1) {
@@ -339,22 +359,15 @@ __device__ __forceinline__ uint64_t draw_partner(const ZipfConsts& zc, const flo
         const uint64_t x = mulhi64(((uint64_t)w3 << 32) | (w2 & ~15u), n - 1);
         return x + (x >= i);
     }
-    const uint64_t N = n - 1;
-    uint64_t k = 1;
-    bool ok = zipf_trial(zc, T, B, N, w3, k);
-    for (uint32_t blk = 1; !ok && blk < 17; ++blk) {  // trials 1..63
+    uint64_t j = 0;
+    if (partner_trial(zc, T, B, n, i, w3, j) || partner_trial(zc, T, B, n, i, w2 & ~15u, j)) return j;
+    for (uint32_t blk = 1; blk <= 16; ++blk) {  // trials 2..63
         const uint4 x = philox4x32_10(make_uint4(c0, c1, t, blk), key0, key1);
-        ok = zipf_trial(zc, T, B, N, x.x, k) || zipf_trial(zc, T, B, N, x.y, k) ||
-             zipf_trial(zc, T, B, N, x.z, k) || (blk < 16 && zipf_trial(zc, T, B, N, x.w, k));
+        if (partner_trial(zc, T, B, n, i, x.x, j) || partner_trial(zc, T, B, n, i, x.y, j) ||
+            (blk < 16 && (partner_trial(zc, T, B, n, i, x.z, j) || partner_trial(zc, T, B, n, i, x.w, j))))
+            return j;
     }
-    if (!ok) k = 1;
-    const bool fwd = (w2 >> 1) & 1u;
-    const bool can_fwd = i + k < n, can_bwd = i >= k;
-    if (fwd && can_fwd) return i + k;
-    if (!fwd && can_bwd) return i - k;
-    if (can_fwd) return i + k;
-    if (can_bwd) return i - k;
-    return (n - 1 - i > i) ? n - 1 : 0;
+    return i + 1 < n ? i + 1 : i - 1;
 }
 
 __device__ __forceinline__ uint4 pair_block(const SamplerArgs& a, uint64_t u) {
@@ -381,10 +394,11 @@ __device__ __forceinline__ Pair pair_from_block(const SamplerArgs& a, const Path
 }
 
 // Draw the pair of update u in iteration t (Algorithm 1, lines 5-11). One
-// Philox block serves the whole draw: w0, w1 pick the step, bits 0-3 of w2
-// are the coins, w3 feeds the first power-law trial or, with the upper 28
-// bits of w2, the uniform partner. Later blocks are drawn only after a
-// power-law trial rejects (about 1 update in 1000).
+// Philox block serves the whole draw: w0, w1 pick the step, bits 0, 2 and 3
+// of w2 are the cooling and endpoint coins, w3 and the upper 28 bits of w2
+// feed the uniform partner or the first two power-law trials. Later blocks
+// are drawn only after both of those trials fail (about 1 power-law draw in
+// 200).
 __device__ __forceinline__ Pair draw_pair(const SamplerArgs& a, const PathTable& pt, uint64_t u) {
     const uint4 w = pair_block(a, u);
     return pair_from_block(a, pt, u, w, w.z & 1u);

@@ -106,8 +106,13 @@ def _sweep_check(G, g, xy, t, eta, seed, u0, count):
         mu = np.minimum(eta / (d * d), 1.0)
     scale = np.where(s["skip"] == 0, mu * (mag + d) / 2, 0.0)
     err = np.abs(got - want).max(axis=1)
-    # per update: |dv_gpu - dv_ref| <= 1e-5 * mu (|v_i - v_j| + d_ref) / 2
-    bad = err > 1e-5 * scale + 1e-30
+    # per update: |dv_gpu - dv_ref| <= 1e-5 * mu (|v_i - v_j| + d_ref) / 2, widened
+    # where the two points nearly coincide: FP32 x offsets from the anchors
+    # (up to 8 nt each) carry an absolute rounding of about 2^-24 * 16 whatever
+    # the separation, which the move's direction (v_i - v_j) / |v_i - v_j| inherits
+    with np.errstate(divide="ignore", invalid="ignore"):
+        widen = np.where(mag > 0, 1.0 + 16.0 / mag, 1.0)
+    bad = err > 1e-5 * scale * widen + 1e-30
     assert not bad.any(), (np.nonzero(bad)[0][:5], err[bad][:5], scale[bad][:5])
     # skipped updates move nothing on both sides
     assert np.all(got[s["skip"] != 0] == 0) and np.all(want[s["skip"] != 0] == 0)
