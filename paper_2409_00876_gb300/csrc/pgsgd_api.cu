@@ -567,7 +567,8 @@ int pgsgd_layout(pgsgd_graph* g, uint32_t iter_max, const double* eta, double et
     int64_t cap = g->max_concurrent;
     if (cap == -1) cap = std::max<int64_t>(2048, (int64_t)g->n_nodes / 2);
     if (cap > 0) {
-        const int64_t per_block = (int64_t)g->block * (g->drf > 1 ? 1 : g->upt);
+        // the cap counts updates: a thread keeps upt updates, or one selection of drf updates, in flight
+        const int64_t per_block = (int64_t)g->block * (g->drf > 1 ? g->drf : g->upt);
         const int64_t gmax = std::max<int64_t>(1, cap / per_block);
         if (gmax < grid) grid = (int)gmax;
     }
