@@ -277,3 +277,25 @@ def test_full_batch_in_the_benchmarked_schedule():
     m = np.array([r["mean"] for r in st])
     m0 = np.array([r["mean"] for r in init])
     assert np.all(np.isfinite(m)) and np.median(m / m0) < 1.5 and np.all(m < 10 * m0.max())
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_per_graph_learning_rates_reach_their_graphs(mode):
+    """Graphs are scheduled in rank order (most updates first); the caller's
+    per-graph eta rows must still reach the right graphs: a graph given
+    eta = 0 in every iteration keeps its layout exactly, the others move."""
+    from paper_2409_00876_gb300.batch import Batch
+    gs = [make_graph("tiny", gen_seed=s, backbone=b, paths=p) for s, b, p in [(3, 400, 3), (4, 2500, 6), (5, 1200, 4)]]
+    arr = concat(gs)
+    B = Batch.from_arrays(arr)
+    B.set_option("mode", mode)
+    eta = np.stack([O.eta_schedule(T, O.default_eta_max(g)) for g in gs])
+    for frozen in range(len(gs)):
+        e = eta.copy()
+        e[frozen] = 0.0
+        B.set_coords(arr.init_xy)
+        B.layout(T, seeds=[7, 8, 9], eta=e, theta=THETA)
+        xy = B.get_coords()
+        for k in range(len(gs)):
+            same = np.array_equal(arr.graph_xy(xy, k), arr.graph_xy(arr.init_xy, k))
+            assert same == (k == frozen), (mode, frozen, k)
