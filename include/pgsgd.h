@@ -364,6 +364,17 @@ int pgsgd_stress_noalloc(const uint32_t *node_len, uint32_t n_nodes,
                          uint32_t samples_per_step, uint64_t seed,
                          pgsgd_stress_result *out, void *cuda_stream);
 
+/*
+ * Measurement helper, no counterpart in the paper: the L2 read bandwidth of
+ * the current GPU in GB/s (*gbs, host), the ceiling for graphs whose records
+ * fit in L2. Allocates a `bytes` buffer (1 MiB..1 GiB; keep it below the L2
+ * size), warms it into L2, then times `reps` (1..1000) passes of mode 0 =
+ * streaming 16-byte vector loads (bytes counted as read) or mode 1 = random
+ * 16-byte loads, each counted as the 32-byte sector it costs. Synchronous;
+ * frees everything it allocated.
+ */
+int pgsgd_l2_bandwidth(uint64_t bytes, uint32_t reps, int mode, double *gbs, void *cuda_stream);
+
 /* Message of the calling thread's last failure ("" if none). */
 const char *pgsgd_last_error(void);
 

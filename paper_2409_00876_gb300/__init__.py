@@ -15,7 +15,7 @@ import numpy as np
 from . import _native as N
 from ._native import PgsgdError, StressResult
 
-__all__ = ["Graph", "PgsgdError", "StressResult", "SAMPLE_DTYPE", "load_library"]
+__all__ = ["Graph", "PgsgdError", "StressResult", "SAMPLE_DTYPE", "load_library", "l2_bandwidth"]
 
 SAMPLE_DTYPE = np.dtype([("g", "<u8"), ("i", "<u8"), ("j", "<u8"), ("d_ref", "<i8"),
                          ("path", "<u4"), ("cooling", "u1"), ("e_i", "u1"),
@@ -24,6 +24,14 @@ SAMPLE_DTYPE = np.dtype([("g", "<u8"), ("i", "<u8"), ("j", "<u8"), ("d_ref", "<i
 
 def load_library():
     return N.load()
+
+
+def l2_bandwidth(bytes_=64 << 20, reps=20, mode=0, stream=None):
+    """Measured L2 read bandwidth in GB/s (mode 0 streaming, 1 random 16-byte loads)."""
+    lib = N.load()
+    out = C.c_double()
+    N.check(lib.pgsgd_l2_bandwidth(int(bytes_), int(reps), int(mode), C.byref(out), stream or _current_stream()))
+    return out.value
 
 
 def _is_torch(x):

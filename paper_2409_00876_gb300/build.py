@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpgsgd.so")
 SOURCES = ["pgsgd_kernels.cu", "pgsgd_api.cu", "pgsgd_noalloc.cu", "pgsgd_grad.cu", "pgsgd_full.cu",
-           "pgsgd_batch.cu"]
+           "pgsgd_batch.cu", "pgsgd_probe.cu"]
 HEADERS = ["pgsgd_device.cuh", "pgsgd_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",

@@ -84,3 +84,11 @@ def test_product_path_has_no_cpu_fallback():
     src = open(pkg.__file__).read() + open(N.__file__).read()
     assert "oracle" not in src.replace("oracle.", "")
     assert "oracle" not in {m.split(".")[0] for m in sys.modules if m.startswith("paper_2409")}
+
+
+def test_l2_probe_rejects_bad_arguments_without_touching_the_gpu():
+    import paper_2409_00876_gb300 as pg
+    from paper_2409_00876_gb300 import PgsgdError
+    for kw in [dict(bytes_=1 << 10), dict(bytes_=1 << 31), dict(reps=0), dict(mode=2)]:
+        with pytest.raises(PgsgdError):
+            pg.l2_bandwidth(**kw)
