@@ -13,18 +13,28 @@
 namespace pgsgd {
 namespace {
 
+// Four independent 16-byte loads in flight per thread; a warp reads 512
+// contiguous bytes per load instruction.
 __global__ void l2_stream_kernel(const uint4* __restrict__ buf, uint64_t n, uint32_t reps, uint32_t* out) {
     uint32_t acc = 0;
     const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     for (uint32_t r = 0; r < reps; ++r) {
-        for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < n; k += nthr) {
-            uint4 v;
-            asm volatile("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];"
-                         : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(buf + k));
-            acc ^= v.x ^ v.w;
+        for (uint64_t k = tid; k < n; k += 4 * nthr) {
+            uint4 v[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const uint64_t idx = k + m * nthr;
+                v[m] = make_uint4(0u, 0u, 0u, 0u);
+                if (idx < n)
+                    asm volatile("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];"
+                                 : "=r"(v[m].x), "=r"(v[m].y), "=r"(v[m].z), "=r"(v[m].w) : "l"(buf + idx));
+            }
+#pragma unroll
+            for (int m = 0; m < 4; ++m) acc ^= v[m].x ^ v[m].w;
         }
     }
-    out[blockIdx.x * (uint64_t)blockDim.x + threadIdx.x] = acc;
+    out[tid] = acc;
 }
 
 __device__ __forceinline__ uint64_t splitmix(uint64_t x) {
