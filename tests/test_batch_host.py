@@ -81,3 +81,51 @@ def test_batch_of_one_graph_matches_its_arrays():
     b = concat([g])
     np.testing.assert_array_equal(b.path_off, g.path_off)
     assert list(b.graph_node_off) == [0, g.n_nodes]
+
+
+class _FakeBatch:
+    """Stands in for a Batch on the CPU: the time of a layout is a made-up
+    function of the options, so the autotuner's search can be checked."""
+
+    def __init__(self, landscape, start):
+        self.opts = dict(start, timing=0)
+        self.landscape = landscape
+        self.calls = 0
+        self._ms = 0.0
+
+    def get_option(self, k):
+        return self.opts[k]
+
+    def set_option(self, k, v):
+        self.opts[k] = v
+
+    def set_coords(self, xy):
+        pass
+
+    def layout(self, *a, **k):
+        self.calls += 1
+        self._ms = self.landscape(self.opts)
+
+    def timing_read(self, reset=True):
+        ms, self._ms = self._ms, 0.0
+        return ms, 1, 1
+
+
+def test_autotune_descends_to_the_best_schedule_and_leaves_it_set():
+    from paper_2409_00876_gb300.batch import autotune
+    space = dict(mode=[0, 1], pipeline=[0, 1], updates_per_thread=[2, 1, 4], block=[256, 128],
+                 chunk=[16384, 4096, 65536])
+    best = dict(mode=1, pipeline=0, updates_per_thread=4, block=128, chunk=65536)
+    cost = dict(mode=3.0, pipeline=1.0, updates_per_thread=2.0, block=0.5, chunk=0.25)
+
+    def landscape(o):  # separable: every coordinate off its best value adds its own penalty
+        return 100.0 + sum(0.0 if o[k] == best[k] else cost[k] for k in space)
+
+    b = _FakeBatch(landscape, dict(mode=0, pipeline=0, updates_per_thread=2, block=256, chunk=16384))
+    got, table = autotune(b, None, space=space)
+    assert got == best
+    assert {k: b.opts[k] for k in space} == best
+    assert b.opts["timing"] == 0
+    # every trial timed once after one untimed run; no trial repeated
+    assert len(table) == len(set(table))
+    assert b.calls == 2 * len(table)
