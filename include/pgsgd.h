@@ -80,7 +80,9 @@ typedef enum pgsgd_option {
     /* Register budget of the update kernel: the number of resident 256-thread
      * blocks per SM its registers must allow (1 = compiler's choice; the
      * compiled variants are 1, 4, 6 for 1 update per thread, 1, 3, 4 for 2
-     * and 1, 2, 3 for 4). Default 1. */
+     * and 1, 2, 3 for 4; the pipelined loop: 1, 3 for 1 and 1, 2 for 2).
+     * Default 0 = automatic: 3 for the plain loop at 2 updates per thread
+     * (80 registers, no spills), else 1. */
     PGSGD_OPT_MIN_BLOCKS = 10,
     /* L2 fetch granularity in bytes set on the current context before each
      * layout (cudaLimitMaxL2FetchGranularity; 0 = leave it unchanged, the

@@ -409,7 +409,7 @@ int pgsgd_set_option(pgsgd_graph* g, int option, int64_t v) {
             g->max_concurrent = v;
             return PGSGD_OK;
         case PGSGD_OPT_MIN_BLOCKS:
-            if (v < 1 || v > 6) return fail(PGSGD_EINVAL, "min blocks must be in [1, 6]");
+            if (v < 0 || v > 6) return fail(PGSGD_EINVAL, "min blocks must be in [0, 6]");
             g->min_blocks = (int)v;
             return PGSGD_OK;
         case PGSGD_OPT_STORE_MODE:
@@ -579,7 +579,9 @@ int pgsgd_layout(pgsgd_graph* g, uint32_t iter_max, const double* eta, double et
     L.block = g->block;
     L.grid = grid;
     L.upt = g->upt;
-    L.minb = g->min_blocks;
+    // automatic register budget: 3 resident blocks per SM (80 registers, no
+    // spills) for the plain loop at 2 updates per thread, measured 3 % faster
+    L.minb = g->min_blocks ? g->min_blocks : (g->upt == 2 && !g->pipeline ? 3 : 1);
     L.store_mode = g->store_mode;
     L.l2_hints = g->l2_hints != 0;
     L.pf64 = g->pf64;

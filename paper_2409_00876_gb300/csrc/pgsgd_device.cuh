@@ -98,6 +98,20 @@ __device__ __forceinline__ NodeRec load_node(const NodeRec* p, uint64_t pol, boo
     return r;
 }
 
+// One endpoint (e = 0 start, 1 end) of a node record: an 8-byte read of the
+// point a move needs (the same 32-byte sector as the whole record).
+__device__ __forceinline__ float2 load_point(const NodeRec* p, uint32_t e, uint64_t pol, bool pf64 = false) {
+    float2 r;
+    const float* q = &p->sx + 2 * e;
+    if (pf64)
+        asm volatile("ld.global.cg.L2::cache_hint.L2::64B.v2.f32 {%0,%1}, [%2], %3;"
+                     : "=f"(r.x), "=f"(r.y) : "l"(q), "l"(pol));
+    else
+        asm volatile("ld.global.cg.L2::cache_hint.v2.f32 {%0,%1}, [%2], %3;"
+                     : "=f"(r.x), "=f"(r.y) : "l"(q), "l"(pol));
+    return r;
+}
+
 // Write one moved point (8 bytes) by replacing it: a 64-bit atomic exchange
 // executed at L2 (last writer wins, like the paper's racy stores, but on
 // GB300 several times faster than any st.global form for this pattern).
@@ -519,17 +533,18 @@ __device__ __forceinline__ void load_trip_steps(const StepRec* __restrict__ step
     }
 }
 
-// Node-record loads, the moves of Algorithm 1, lines 12-15, and the stores.
+// Endpoint loads, the moves of Algorithm 1, lines 12-15, and the stores.
+// Only the chosen endpoint of each node is read (8 bytes, 2 registers).
 template <int UPT>
 __device__ __forceinline__ void finish_trip(NodeRec* __restrict__ nodes, const TripDraws<UPT>& d,
                                             const StepRec (&si)[UPT], const StepRec (&sj)[UPT], const UpdateOpts& o,
                                             uint64_t pol_keep) {
-    NodeRec na[UPT], nb[UPT];
+    float2 va[UPT], vb[UPT];
 #pragma unroll
     for (int k = 0; k < UPT; ++k) {
         if (d.act[k]) {
-            na[k] = load_node(nodes + step_node(si[k]), pol_keep, o.pf64 & 2);
-            nb[k] = load_node(nodes + step_node(sj[k]), pol_keep, o.pf64 & 2);
+            va[k] = load_point(nodes + step_node(si[k]), (d.w2[k] >> 2) & 1u, pol_keep, o.pf64 & 2);
+            vb[k] = load_point(nodes + step_node(sj[k]), (d.w2[k] >> 3) & 1u, pol_keep, o.pf64 & 2);
         }
     }
 #pragma unroll
@@ -539,23 +554,19 @@ __device__ __forceinline__ void finish_trip(NodeRec* __restrict__ nodes, const T
         const int64_t pa = endpoint_pos(si[k], ea), pb = endpoint_pos(sj[k], eb);
         const int64_t dd = pa > pb ? pa - pb : pb - pa;
         if (dd == 0) continue;
-        const Move m = pair_move(na[k], si[k].ax, ea, nb[k], sj[k].ax, eb, dd, o.eta);
+        const Move m = point_move(va[k].x, va[k].y, si[k].ax, vb[k].x, vb[k].y, sj[k].ax, dd, o.eta);
         if (!m.moved) continue;
         float* pa_ptr = &nodes[step_node(si[k])].sx + 2 * ea;
         float* pb_ptr = &nodes[step_node(sj[k])].sx + 2 * eb;
         if (o.atomic) {
             atomicAdd(reinterpret_cast<float2*>(pa_ptr), make_float2(m.dxi, m.dyi));
             atomicAdd(reinterpret_cast<float2*>(pb_ptr), make_float2(m.dxj, m.dyj));
+        } else if (o.store_mode == 0) {
+            *reinterpret_cast<float2*>(pa_ptr) = make_float2(va[k].x + m.dxi, va[k].y + m.dyi);
+            *reinterpret_cast<float2*>(pb_ptr) = make_float2(vb[k].x + m.dxj, vb[k].y + m.dyj);
         } else {
-            const float xa = ea ? na[k].ex : na[k].sx, ya = ea ? na[k].ey : na[k].sy;
-            const float xb = eb ? nb[k].ex : nb[k].sx, yb = eb ? nb[k].ey : nb[k].sy;
-            if (o.store_mode == 0) {
-                *reinterpret_cast<float2*>(pa_ptr) = make_float2(xa + m.dxi, ya + m.dyi);
-                *reinterpret_cast<float2*>(pb_ptr) = make_float2(xb + m.dxj, yb + m.dyj);
-            } else {
-                exchange_point(pa_ptr, xa + m.dxi, ya + m.dyi, pol_keep);
-                exchange_point(pb_ptr, xb + m.dxj, yb + m.dyj, pol_keep);
-            }
+            exchange_point(pa_ptr, va[k].x + m.dxi, va[k].y + m.dyi, pol_keep);
+            exchange_point(pb_ptr, vb[k].x + m.dxj, vb[k].y + m.dyj, pol_keep);
         }
     }
 }

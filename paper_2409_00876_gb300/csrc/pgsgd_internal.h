@@ -150,7 +150,7 @@ struct pgsgd_graph {
     int rebase = 1;
     int timing = 0;
     int64_t max_concurrent = -1;  // -1 = automatic
-    int min_blocks = 1;
+    int min_blocks = 0;   // 0 = automatic: 3 blocks per SM for the plain loop at 2 updates per thread, else 1
     int l2_fetch = 0;
     int store_mode = 1;  // 64-bit atomic exchange: measured fastest replace-store
     int l2_hints = 1;
