@@ -53,13 +53,15 @@ def test_reuse_draws_are_bit_exact(pg, mid, drf, srf, wm):
         _same(got.ravel(), want.ravel())
 
 
-def _sparse_iteration(pg, g, drf, wm, srf, t=10, seed=3):
+def _sparse_iteration(pg, g, drf, wm, srf, t=10, seed=3, **opts):
     """One iteration with so few updates that nodes rarely meet twice: GPU
     kernel vs the oracle's sequential mirror from the same layout."""
     G = pg.Graph.from_synth(g)
     G.set_option("drf", drf)
     G.set_option("srf", srf)
     G.set_option("warp_merge", wm)
+    for k, v in opts.items():
+        G.set_option(k, v)
     G.set_coords(g.init_xy)
     G.layout(T, theta=0.99, seed=seed, iter_begin=t, iter_end=t + 1)
     got = G.get_coords()
@@ -69,10 +71,16 @@ def _sparse_iteration(pg, g, drf, wm, srf, t=10, seed=3):
     return got, want, moved
 
 
-@pytest.mark.parametrize("drf,wm", [(1, 0), (1, 1), (2, 0), (4, 1), (8, 0)])
-def test_kernel_updates_match_the_oracle_on_a_sparse_iteration(pg, mid, drf, wm):
+@pytest.mark.parametrize("drf,wm,opts", [
+    (1, 0, {}), (1, 1, {}), (2, 0, {}), (4, 1, {}), (8, 0, {}),
+    # the other compiled shapes of the plain update loop
+    (1, 0, dict(pipeline=1)), (1, 0, dict(pipeline=1, updates_per_thread=1)),
+    (1, 0, dict(updates_per_thread=1)), (1, 0, dict(updates_per_thread=4)), (1, 0, dict(min_blocks=1)),
+    (1, 0, dict(updates_per_thread=1, min_blocks=4)), (1, 1, dict(updates_per_thread=4)),
+])
+def test_kernel_updates_match_the_oracle_on_a_sparse_iteration(pg, mid, drf, wm, opts):
     srf = -(-10 * mid.n_steps // 1024)  # about 1024 selections on 220 k nodes
-    got, want, moved = _sparse_iteration(pg, mid, drf, wm, srf)
+    got, want, moved = _sparse_iteration(pg, mid, drf, wm, srf, **opts)
     assert moved > 0.5 * 1024 * drf
     init = mid.init_xy
     gpu_touched = np.any(got != init, axis=1)
@@ -81,7 +89,7 @@ def test_kernel_updates_match_the_oracle_on_a_sparse_iteration(pg, mid, drf, wm)
     assert (gpu_touched != orc_touched).sum() <= 1e-3 * orc_touched.sum() + 2
     close = np.all(np.abs(got - want) <= 1e-2 + 1e-5 * np.abs(want), axis=1)
     frac = close[orc_touched].mean()
-    print("drf", drf, "wm", wm, "touched", orc_touched.sum(), "close", frac)
+    print("drf", drf, "wm", wm, opts, "touched", orc_touched.sum(), "close", frac)
     assert frac >= 0.99, frac
 
 
