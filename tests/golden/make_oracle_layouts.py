@@ -27,7 +27,7 @@ OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_layouts.j
 PLAN = {
     # name: (layout seeds, stress samples per step, stress seed)
     "tiny": ([1, 2, 3, 4, 5], 100, 7),
-    "mid": ([1, 2], 100, 7),
+    "mid": ([1, 2, 3, 4, 5, 6], 100, 7),
     "chrom": ([1], 10, 7),
 }
 
