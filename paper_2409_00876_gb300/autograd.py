@@ -38,16 +38,17 @@ def sampled_stress(xy, graph, n_pairs=10_000_000, seed=1):
     return SampledStress.apply(xy, graph, n_pairs, seed)
 
 
-def refine(graph, xy, steps=200, lr=0.05, n_pairs=10_000_000, seed=1, eval_fn=None):
-    """Full-batch gradient refinement of a layout with Adam on the
-    differentiable sampled stress. Returns the refined layout and the
-    objective's trace (first and last values, and eval_fn's if given)."""
+def refine(graph, xy, steps=200, lr=0.05, n_pairs=10_000_000, seed=1, resample=False):
+    """Gradient refinement of a layout with Adam on the differentiable sampled
+    stress. Full batch (default): the same n_pairs pairs every step (seed);
+    resample=True draws a fresh set each step (seed + step), a stochastic
+    variant. Returns the refined layout and the objective's value per step."""
     x = xy.detach().clone().requires_grad_(True)
     opt = torch.optim.Adam([x], lr=lr)
     trace = []
-    for _ in range(steps):
+    for k in range(steps):
         opt.zero_grad()
-        f = sampled_stress(x, graph, n_pairs, seed)
+        f = sampled_stress(x, graph, n_pairs, seed + k if resample else seed)
         f.backward()
         opt.step()
         trace.append(float(f.detach()))
