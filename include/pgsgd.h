@@ -55,7 +55,9 @@ typedef enum pgsgd_option {
     /* Update-kernel launch shape: threads per block (64..256, multiple of
      * 32; default 256), blocks per SM in the grid (default 32: many short
      * blocks let the block scheduler balance the two dies), and
-     * updates each thread keeps in flight per loop trip (1, 2 or 4; default 2). */
+     * updates each thread keeps in flight per loop trip (1, 2 or 4; default 1,
+     * which with 4 resident blocks per SM ran the chromosome layout 2.7 %
+     * faster than 2 with 3). */
     PGSGD_OPT_BLOCK = 3,
     PGSGD_OPT_BLOCKS_PER_SM = 4,
     PGSGD_OPT_UPDATES_PER_THREAD = 5,
@@ -81,8 +83,8 @@ typedef enum pgsgd_option {
      * blocks per SM its registers must allow (1 = compiler's choice; the
      * compiled variants are 1, 4, 6 for 1 update per thread, 1, 3, 4 for 2
      * and 1, 2, 3 for 4; the pipelined loop: 1, 3 for 1 and 1, 2 for 2).
-     * Default 0 = automatic: 3 for the plain loop at 2 updates per thread
-     * (80 registers, no spills), else 1. */
+     * Default 0 = automatic: for the plain loop 4 at 1 update per thread and
+     * 3 at 2 (no spills), else 1. */
     PGSGD_OPT_MIN_BLOCKS = 10,
     /* L2 fetch granularity in bytes set on the current context before each
      * layout (cudaLimitMaxL2FetchGranularity; 0 = leave it unchanged, the

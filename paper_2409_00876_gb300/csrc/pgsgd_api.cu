@@ -579,9 +579,10 @@ int pgsgd_layout(pgsgd_graph* g, uint32_t iter_max, const double* eta, double et
     L.block = g->block;
     L.grid = grid;
     L.upt = g->upt;
-    // automatic register budget: 3 resident blocks per SM (80 registers, no
-    // spills) for the plain loop at 2 updates per thread, measured 3 % faster
-    L.minb = g->min_blocks ? g->min_blocks : (g->upt == 2 && !g->pipeline ? 3 : 1);
+    // automatic register budget for the plain loop: 4 resident blocks per SM
+    // at 1 update per thread, 3 at 2 (no spills either way), else the
+    // compiler's choice
+    L.minb = g->min_blocks ? g->min_blocks : g->pipeline ? 1 : g->upt == 1 ? 4 : g->upt == 2 ? 3 : 1;
     L.store_mode = g->store_mode;
     L.l2_hints = g->l2_hints != 0;
     L.pf64 = g->pf64;

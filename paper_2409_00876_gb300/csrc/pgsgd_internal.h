@@ -145,12 +145,12 @@ struct pgsgd_graph {
     int updates_per_step = 10;
     int block = 256;
     int blocks_per_sm = 32;
-    int upt = 2;
+    int upt = 1;
     int atomic = 0;
     int rebase = 1;
     int timing = 0;
     int64_t max_concurrent = -1;  // -1 = automatic
-    int min_blocks = 0;   // 0 = automatic: 3 blocks per SM for the plain loop at 2 updates per thread, else 1
+    int min_blocks = 0;   // 0 = automatic register budget (plain loop: 4 blocks per SM at 1 update per thread, 3 at 2)
     int l2_fetch = 0;
     int store_mode = 1;  // 64-bit atomic exchange: measured fastest replace-store
     int l2_hints = 1;

@@ -74,9 +74,9 @@ def _sparse_iteration(pg, g, drf, wm, srf, t=10, seed=3, **opts):
 @pytest.mark.parametrize("drf,wm,opts", [
     (1, 0, {}), (1, 1, {}), (2, 0, {}), (4, 1, {}), (8, 0, {}),
     # the other compiled shapes of the plain update loop
-    (1, 0, dict(pipeline=1)), (1, 0, dict(pipeline=1, updates_per_thread=1)),
-    (1, 0, dict(updates_per_thread=1)), (1, 0, dict(updates_per_thread=4)), (1, 0, dict(min_blocks=1)),
-    (1, 0, dict(updates_per_thread=1, min_blocks=4)), (1, 1, dict(updates_per_thread=4)),
+    (1, 0, dict(pipeline=1)), (1, 0, dict(pipeline=1, updates_per_thread=2)),
+    (1, 0, dict(updates_per_thread=2)), (1, 0, dict(updates_per_thread=4)), (1, 0, dict(min_blocks=1)),
+    (1, 0, dict(min_blocks=6)), (1, 0, dict(updates_per_thread=2, min_blocks=1)), (1, 1, dict(updates_per_thread=4)),
 ])
 def test_kernel_updates_match_the_oracle_on_a_sparse_iteration(pg, mid, drf, wm, opts):
     srf = -(-10 * mid.n_steps // 1024)  # about 1024 selections on 220 k nodes
