@@ -133,7 +133,9 @@ int pgsgd_batch_get_coords(pgsgd_batch *b, double *xy, int on_device, void *cuda
  *          nucleotides)^2 and eta_min = 0.01
  *   theta  Zipf exponent in [0, 4], the same for all graphs
  *   seeds  host [G] Philox keys, one per graph
- * Asynchronous in modes 0 and 2, synchronous in mode 1 (see
+ * The call uploads its per-graph tables from the host first, so it waits for
+ * work already queued on the stream; the layout itself is then queued
+ * asynchronously in modes 0 and 2 and waited for in mode 1 (see
  * PGSGD_BOPT_MODE).
  */
 int pgsgd_batch_layout(pgsgd_batch *b, uint32_t iter_max, const double *eta,
