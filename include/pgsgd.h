@@ -37,7 +37,7 @@ typedef enum pgsgd_status {
     PGSGD_ENOMEM = 3,   /* host or device allocation failed */
     PGSGD_ECUDA = 4,    /* a CUDA call or kernel failed */
     PGSGD_ETIMEOUT = 5, /* a device-side bounded wait expired */
-    PGSGD_EDEVICE = 6   /* a device-side bounds check tripped */
+    PGSGD_EDEVICE = 6   /* reserved: device-side checks report EINVAL / ERANGE */
 } pgsgd_status;
 
 /* Options for pgsgd_set_option / pgsgd_get_option. */
@@ -61,11 +61,12 @@ typedef enum pgsgd_option {
     PGSGD_OPT_BLOCK = 3,
     PGSGD_OPT_BLOCKS_PER_SM = 4,
     PGSGD_OPT_UPDATES_PER_THREAD = 5,
-    /* 0 = plain stores of the moved points (last writer wins, as in the
-     * paper's kernels; default), 1 = vector atomic adds of the moves. Atomic
-     * adds sum colliding full-rate (mu = 1) moves, which overshoot; on small
-     * graphs under a full grid that diverges, so keep 0 unless the
-     * concurrency cap makes collisions rare. */
+    /* 0 = replace the moved points (last writer wins, as in the paper's
+     * kernels; the form of the write is PGSGD_OPT_STORE_MODE; default),
+     * 1 = vector atomic adds of the moves. Atomic adds sum colliding
+     * full-rate (mu = 1) moves, which overshoot; on small graphs under a full
+     * grid that diverges, so keep 0 unless the concurrency cap makes
+     * collisions rare. */
     PGSGD_OPT_ATOMIC_UPDATES = 6,
     /* 1 = after each iteration, move the x anchor of every node whose start
      * offset has drifted past 8 to the rounded start point, so the FP32
@@ -76,8 +77,9 @@ typedef enum pgsgd_option {
      * launching stream; read them with pgsgd_timing_read. Default 0. */
     PGSGD_OPT_TIMING = 8,
     /* Concurrency cap: the update kernel's grid is shrunk so that at most this
-     * many updates are in flight at once (0 = no cap). Small graphs under a
-     * full GB300 grid would otherwise see many simultaneous updates per node. */
+     * many updates are in flight at once (0 = no cap; -1, the default,
+     * = max(2048, n_nodes / 2)). Small graphs under a full GB300 grid would
+     * otherwise see many simultaneous updates per node. */
     PGSGD_OPT_MAX_CONCURRENT = 9,
     /* Register budget of the update kernel: the number of resident 256-thread
      * blocks per SM its registers must allow (1 = compiler's choice; the
@@ -117,7 +119,7 @@ typedef enum pgsgd_option {
     /* Warp merging (Section V-B3): 1 = the cooling coin of update u is bit 0
      * of w2 of update 32 floor(u / 32), so a warp's 32 consecutive updates
      * take the same branch (one control draw, shared by shuffle). Draws and
-     * moves otherwise unchanged. Default 0. */
+     * moves otherwise unchanged. Needs PGSGD_OPT_PIPELINE = 0. Default 0. */
     PGSGD_OPT_WARP_MERGE = 16,
     /* Warp-level data reuse (Section VII-D). Data reuse factor DRF (1, 2, 4
      * or 8; default 1 = off): every selection performs DRF updates; the 32
