@@ -224,7 +224,9 @@ int pgsgd_get_coords(pgsgd_graph *g, double *xy, int on_device, void *cuda_strea
  * N = updates_per_step * S lock-free updates at learning rate eta_t.
  *   eta      host array of iter_max rates, or NULL for the annealing of
  *            Zheng et al.: eta_t = eta_max * exp(-lambda t),
- *            lambda = ln(eta_max / eta_min) / (T - 1)
+ *            lambda = ln(eta_max / eta_min) / (T - 1); every rate, given
+ *            or computed, must be finite and >= 0 (PGSGD_EINVAL otherwise,
+ *            before any launch)
  *   eta_max  <= 0 selects (longest path in nucleotides)^2
  *   eta_min  <= 0 selects 0.01
  *   theta    Zipf exponent of the power-law pair choice, in [0, 4]

@@ -130,7 +130,8 @@ int pgsgd_batch_get_coords(pgsgd_batch *b, double *xy, int on_device, void *cuda
  * (Algorithm 1).
  *   eta    host [G][iter_max] learning rates, or NULL: per graph, the
  *          annealing of pgsgd_layout with eta_max = (graph's longest path in
- *          nucleotides)^2 and eta_min = 0.01
+ *          nucleotides)^2 and eta_min = 0.01; given rates must be finite
+ *          and >= 0 (PGSGD_EINVAL otherwise, before any launch)
  *   theta  Zipf exponent in [0, 4], the same for all graphs
  *   seeds  host [G] Philox keys, one per graph
  * The call uploads its per-graph tables from the host first, so it waits for

@@ -551,6 +551,10 @@ int pgsgd_layout(pgsgd_graph* g, uint32_t iter_max, const double* eta, double et
             for (uint32_t t = 0; t < iter_max; ++t) sched[t] = emax * std::exp(-lambda * (double)t);
         }
     }
+    // a negative rate moves a pair apart and a NaN poisons both nodes
+    for (uint32_t t = 0; t < iter_max; ++t)
+        if (!(std::isfinite(sched[t]) && sched[t] >= 0.0))
+            return fail(PGSGD_EINVAL, "learning rate %g at iteration %u is not finite and >= 0", sched[t], t);
     const float th = (float)theta;
     rc = ensure_zipf(g, th, st);
     if (rc) return rc;

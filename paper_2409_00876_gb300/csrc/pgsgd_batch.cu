@@ -1031,9 +1031,14 @@ int pgsgd_batch_layout(pgsgd_batch* b, uint32_t iter_max, const double* eta, dou
     if (iter_max == 0) return fail(PGSGD_EINVAL, "iter_max is 0");
     if (iter_begin > iter_end || iter_end > iter_max) return fail(PGSGD_EINVAL, "need iter_begin <= iter_end <= iter_max");
     if (!(theta >= 0.0 && theta <= 4.0)) return fail(PGSGD_EINVAL, "theta %g not in [0, 4]", theta);
+    const uint32_t G = b->n_graphs;
+    if (eta)
+        for (size_t e = 0; e < (size_t)G * iter_max; ++e)
+            if (!(std::isfinite(eta[e]) && eta[e] >= 0.0))
+                return fail(PGSGD_EINVAL, "learning rate %g of graph %zu at iteration %zu is not finite and >= 0",
+                            eta[e], e / iter_max, e % iter_max);
     if (iter_begin == iter_end) return PGSGD_OK;
     cudaStream_t st = S(cuda_stream);
-    const uint32_t G = b->n_graphs;
     const float th = (float)theta;
     if ((rc = ensure_zipf(b->g, th, st))) return rc;
     if ((rc = prepare(b, seeds, st))) return rc;

@@ -241,6 +241,25 @@ def test_create_rejects_a_node_outside_its_graph():
               arr.step_rev, arr.step_pos)
 
 
+def test_batch_layout_rejects_bad_learning_rates_before_any_move():
+    from paper_2409_00876_gb300 import PgsgdError
+    from paper_2409_00876_gb300.batch import Batch
+    gs = [make_graph("tiny"), make_graph("tiny", gen_seed=4, backbone=300, paths=2)]
+    arr = concat(gs)
+    B = Batch.from_arrays(arr)
+    B.set_coords(arr.init_xy)
+    before = B.get_coords()
+    eta = np.tile(np.geomspace(100.0, 0.01, T), (2, 1))
+    for v in [np.nan, -1.0, np.inf]:
+        bad = eta.copy()
+        bad[1, 4] = v
+        with pytest.raises(PgsgdError, match="learning rate"):
+            B.layout(T, seeds=[1, 2], eta=bad)
+    np.testing.assert_array_equal(B.get_coords(), before)
+    B.layout(T, seeds=[1, 2], eta=eta)
+    assert not np.array_equal(B.get_coords(), before)
+
+
 def test_full_batch_in_the_benchmarked_schedule():
     """The 256-graph workload in the autotuned schedule the benchmark times:
     draws of the largest, a middle and the smallest graph are bit-exact with

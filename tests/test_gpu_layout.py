@@ -168,3 +168,26 @@ def test_create_rejects_inconsistent_graphs(pg):
     with pytest.raises(PgsgdError, match="theta"):
         G.set_coords(g.init_xy)
         G.layout(T, theta=5.0)
+
+
+def test_layout_rejects_bad_learning_rates_before_any_move(pg):
+    """A negative or NaN rate would move pairs apart or poison both nodes:
+    the call refuses it before the first launch, so the layout is unchanged."""
+    from paper_2409_00876_gb300 import PgsgdError
+    g = make_graph("tiny")
+    G = pg.Graph.from_synth(g)
+    G.set_coords(g.init_xy)
+    before = G.get_coords()
+    good = np.geomspace(100.0, 0.01, T)
+    for t, v in [(0, np.nan), (T - 1, -1e-3), (7, np.inf)]:
+        eta = good.copy()
+        eta[t] = v
+        with pytest.raises(PgsgdError, match="learning rate"):
+            G.layout(T, eta=eta, seed=3)
+    with pytest.raises(PgsgdError, match="learning rate"):
+        G.layout(T, eta_max=np.inf, seed=3)
+    np.testing.assert_array_equal(G.get_coords(), before)
+    eta = good.copy()
+    eta[-5:] = 0.0  # a zero rate is a valid no-op iteration
+    G.layout(T, eta=eta, seed=3)
+    assert not np.array_equal(G.get_coords(), before)
