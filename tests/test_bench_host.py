@@ -1,0 +1,78 @@
+"""Host logic of the benchmark (no GPU): the reference arm's JSON line on the
+tiny workload, the clock record built from nvidia-smi samples, and the
+roofline arithmetic."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_reference_arm_prints_one_line_of_the_contract():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--config", "tiny",
+                        "--steps", "2", "--warmup", "1", "--ref-budget", "0.2"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "updates/s"
+    assert d["n_gpus"] == 1 and d["steps"] == 2 and d["warmup"] == 1
+    assert d["higher_is_better"] is True and d["scaling"] == "weak" and d["vs_baseline"] is None
+    assert d["dtype"] == "f64" and d["data"] == "synthetic"
+    assert d["config"]["name"] == "tiny" and d["config"]["workload"] == bench.WORKLOADS["tiny"]
+    assert d["value"] > 0
+    # one step is one whole layout: 30 iterations x 10 x S updates at the measured rate
+    from synth import make_graph
+    S = make_graph("tiny").n_steps
+    assert d["ms_per_step"] == pytest.approx(30 * 10 * S / d["value"] * 1e3, rel=1e-9)
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "updates/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_leaves_ranks_above_zero_idle():
+    env = dict(os.environ, WORLD_SIZE="2", RANK="1", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--config", "tiny",
+                        "--steps", "1", "--warmup", "0"], capture_output=True, text=True, timeout=300, cwd=ROOT,
+                       env=env)
+    assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def _sample(sm, smax=2070, reasons=("Not Active",) * 4):
+    return ", ".join([str(sm), str(smax), "900.0", "0x0"] + list(reasons))
+
+
+def test_clock_record_takes_the_median_of_loaded_samples_and_every_reason_seen():
+    lines = [_sample(900), _sample(2070), _sample(2055), _sample(2040, reasons=("Not Active",) * 3 + ("Active",)),
+             "garbage", _sample("[N/A]"), _sample(2070)]
+    c = bench.summarize_clocks(lines)
+    # the idle 900 MHz sample is not under load; the malformed ones are skipped
+    assert c["sm_mhz"] == 2062.5 and c["sm_max_mhz"] == 2070 and c["samples"] == 5
+    assert c["reasons"] == ["sw_power_cap"]
+    hot = bench.summarize_clocks([_sample(1500, reasons=("Active", "Not Active", "Active", "Not Active"))])
+    assert hot["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"] and hot["sm_mhz"] == 1500
+    assert bench.summarize_clocks([])["reasons"] == ["no samples"]
+
+
+def test_roofline_fraction_of_the_hbm_peak():
+    r = bench.roofline_for("chrom", 4000.0, 6778.0, "measured", 6.58e11, 225.0)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] == 6778.0
+    assert r["frac"] == pytest.approx(4000.0 / 6778.0)
+    assert r["bytes_per_update_model"] == bench.BYTES_PER_UPDATE == 192
+    assert r["traffic"] == 6.58e11 and r["launch_ms"] == 225.0
+
+
+def test_peaks_come_from_the_measured_file_when_present():
+    peak, kind = bench.peaks()
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        assert kind == "measured" and peak == float(json.load(open(path))["hbm_gbs"])
+    else:
+        assert (peak, kind) == (6800.0, "fallback")
