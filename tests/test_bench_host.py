@@ -76,3 +76,13 @@ def test_peaks_come_from_the_measured_file_when_present():
         assert kind == "measured" and peak == float(json.load(open(path))["hbm_gbs"])
     else:
         assert (peak, kind) == (6800.0, "fallback")
+
+
+def test_traffic_record_belongs_to_the_current_update_kernel():
+    """The benchmark reports the recorded ncu DRAM traffic only while the update
+    kernel's source hash matches the one the record was taken on."""
+    rec = json.load(open(os.path.join(ROOT, "profiles", "update_kernel_traffic_chrom.json")))
+    assert rec["kernel_rev"] == bench.kernel_revision()
+    per_update = (rec["dram_bytes_read_per_launch"] + rec["dram_bytes_write_per_launch"]) / rec["updates_per_launch"]
+    assert rec["dram_bytes_per_update"] == pytest.approx(per_update, abs=0.01)
+    assert rec["updates_per_launch"] == 10 * 468_635_155  # 10 x S of the chromosome graph
