@@ -73,16 +73,18 @@ def test_layout_stress_matches_oracle(pg, name):
     (the same drawn pairs, applied concurrently). The mean stresses are
     compared; the bar is the larger of 1 % of the oracle's mean and twice the
     standard error that the seed-to-seed and run-to-run spread of both sides
-    implies. With a single oracle run (the chromosome graph) that run is the
-    reference value: the GPU's expected stress, estimated by three repeats,
-    must be within 1 % of it, plus two standard errors of the estimate."""
+    implies. With a single oracle run (the chromosome graph) the GPU's expected
+    stress, estimated by five repeats, must be within 1 % of that run plus two
+    standard errors of the difference: the oracle's run is one draw of a
+    lock-free process too, whose run-to-run variance is taken to be that of one
+    GPU run."""
     gold = _gold(name)
     g = make_graph(name)
     fp = gold["fingerprint"]
     assert (g.n_nodes, g.n_paths, g.n_steps) == (fp["n_nodes"], fp["n_paths"], fp["n_steps"])
     per, sseed = gold["stress_samples_per_step"], gold["stress_seed"]
     ref = np.array([r["stress"] for r in gold["runs"]])
-    reps = 1 if len(ref) > 1 else 3
+    reps = 1 if len(ref) > 1 else 5
     got = []
     for run in gold["runs"]:
         got += [_layout_stress(pg, g, run["seed"], per, sseed)[0]["mean"] for _ in range(reps)]
@@ -91,10 +93,11 @@ def test_layout_stress_matches_oracle(pg, name):
         se = np.sqrt(got.var(ddof=1) / len(got) + ref.var(ddof=1) / len(ref))
         bar = max(0.01 * ref.mean(), 2 * se)
     else:
-        # one oracle run is the reference value: the GPU's expected stress
-        # must lie within 1 % of it, and the repeats estimate that expectation
-        # to within two standard errors
-        bar = 0.01 * ref.mean() + 2 * got.std(ddof=1) / np.sqrt(len(got))
+        # one oracle run: the GPU's expected stress must lie within 1 % of it;
+        # the difference carries the error of the GPU mean and the run-to-run
+        # variance of the oracle's single run (estimated by one GPU run's)
+        v = got.var(ddof=1)
+        bar = 0.01 * ref.mean() + 2 * np.sqrt(v / len(got) + v)
     print(name, got, ref, abs(got.mean() - ref.mean()) / ref.mean(), bar / ref.mean())
     assert abs(got.mean() - ref.mean()) <= bar, (got, ref, bar)
     assert got.max() < 0.5 * gold["init_stress"]
