@@ -8,6 +8,11 @@ generator are called. The GPU tests compare the CUDA layout's stress, under
 the same seeds, against these values.
 
     python tests/golden/make_oracle_layouts.py [--configs mid chrom] [--threads 6]
+    python tests/golden/make_oracle_layouts.py --repeat chrom
+
+--repeat appends one more run of the workload's first seed to its stored
+entry (same oracle source, graph and thread count): a second lock-free run
+under the same seed measures the oracle's own run-to-run spread.
 """
 import argparse
 import json
@@ -49,8 +54,12 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--configs", nargs="+", default=list(PLAN))
     ap.add_argument("--threads", type=int, default=os.cpu_count())
+    ap.add_argument("--repeat", default=None, help="append one run of this workload's first seed")
     args = ap.parse_args()
     data = json.load(open(OUT)) if os.path.exists(OUT) else {}
+    if args.repeat:
+        repeat(data, args.repeat)
+        return
     for name in args.configs:
         seeds, per_step, sseed = PLAN[name]
         g = make_graph(name)
@@ -73,6 +82,25 @@ def main():
             data[name] = entry
             with open(OUT, "w") as f:
                 json.dump(data, f, indent=1)
+
+
+def repeat(data, name):
+    entry = data[name]
+    g = make_graph(name)
+    if entry["fingerprint"] != fingerprint(g) or entry["oracle_sha"] != oracle_sha():
+        raise SystemExit(f"{name}: stored entry is for another graph or oracle source")
+    seed = entry["runs"][0]["seed"]
+    per_step, sseed, threads = entry["stress_samples_per_step"], entry["stress_seed"], entry["oracle_threads"]
+    t0 = time.time()
+    xy, moved = O.layout(g, g.init_xy, T=entry["iterations"], theta=entry["theta"], seed=seed, n_threads=threads)
+    t1 = time.time()
+    st = O.sampled_stress(g, xy, per_step=per_step, seed=sseed, n_threads=threads)
+    print(name, "repeat", seed, st["mean"], round(t1 - t0, 1), "s", flush=True)
+    data = json.load(open(OUT))  # re-read: only this entry changes
+    data[name]["runs"].append(dict(seed=seed, stress=st["mean"], ci_lo=st["ci_lo"], ci_hi=st["ci_hi"],
+                                   n_valid=st["n_valid"], moved=moved, layout_seconds=round(t1 - t0, 1)))
+    with open(OUT, "w") as f:
+        json.dump(data, f, indent=1)
 
 
 if __name__ == "__main__":
