@@ -73,31 +73,28 @@ def test_layout_stress_matches_oracle(pg, name):
     (the same drawn pairs, applied concurrently). The mean stresses are
     compared; the bar is the larger of 1 % of the oracle's mean and twice the
     standard error that the seed-to-seed and run-to-run spread of both sides
-    implies. With a single oracle run (the chromosome graph) the GPU's expected
-    stress, estimated by five repeats, must be within 1 % of that run plus two
-    standard errors of the difference: the oracle's run is one draw of a
-    lock-free process too, whose run-to-run variance is taken to be that of one
-    GPU run."""
+    implies. For the chromosome graph the oracle recorded one seed (each run
+    takes hours): the GPU's expected stress, estimated by five repeats, must be
+    within 1 % of the oracle's mean plus two standard errors of the
+    difference. The oracle's runs are draws of a lock-free process too; their
+    run-to-run variance is the measured one when the record holds repeats,
+    else taken to be that of one GPU run."""
     gold = _gold(name)
     g = make_graph(name)
     fp = gold["fingerprint"]
     assert (g.n_nodes, g.n_paths, g.n_steps) == (fp["n_nodes"], fp["n_paths"], fp["n_steps"])
     per, sseed = gold["stress_samples_per_step"], gold["stress_seed"]
     ref = np.array([r["stress"] for r in gold["runs"]])
-    reps = 1 if len(ref) > 1 else 5
-    got = []
-    for run in gold["runs"]:
-        got += [_layout_stress(pg, g, run["seed"], per, sseed)[0]["mean"] for _ in range(reps)]
-    got = np.array(got)
-    if len(ref) > 1:
+    seeds = [r["seed"] for r in gold["runs"]]
+    if len(set(seeds)) > 1:
+        got = np.array([_layout_stress(pg, g, sd, per, sseed)[0]["mean"] for sd in seeds])
         se = np.sqrt(got.var(ddof=1) / len(got) + ref.var(ddof=1) / len(ref))
         bar = max(0.01 * ref.mean(), 2 * se)
     else:
-        # one oracle run: the GPU's expected stress must lie within 1 % of it;
-        # the difference carries the error of the GPU mean and the run-to-run
-        # variance of the oracle's single run (estimated by one GPU run's)
+        got = np.array([_layout_stress(pg, g, seeds[0], per, sseed)[0]["mean"] for _ in range(5)])
         v = got.var(ddof=1)
-        bar = 0.01 * ref.mean() + 2 * np.sqrt(v / len(got) + v)
+        vo = ref.var(ddof=1) if len(ref) > 1 else v
+        bar = 0.01 * ref.mean() + 2 * np.sqrt(v / len(got) + vo / len(ref))
     print(name, got, ref, abs(got.mean() - ref.mean()) / ref.mean(), bar / ref.mean())
     assert abs(got.mean() - ref.mean()) <= bar, (got, ref, bar)
     assert got.max() < 0.5 * gold["init_stress"]
