@@ -646,16 +646,42 @@ def run_e2e(pg, g, args, dev):
             "phases_s_per_step": {n: round(v / k, 3) for n, v in phases.items()}}
 
 
+def strip_comments(src: str) -> str:
+    """C/C++ source without its comments and with runs of white space folded
+    to one space (string and character literals kept as they are)."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            out.append(" ")
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def kernel_revision():
     """Hash of the update kernel's code (the device helpers and the update
-    kernel's section): a recorded ncu traffic count is only valid for it."""
+    kernel's section, comments and layout of white space left out): a recorded
+    ncu traffic count is only valid for it."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2409_00876_gb300", "csrc")
-    h = hashlib.sha1(open(os.path.join(csrc, "pgsgd_device.cuh"), "rb").read())
+    h = hashlib.sha1(strip_comments(open(os.path.join(csrc, "pgsgd_device.cuh")).read()).encode())
     text = open(os.path.join(csrc, "pgsgd_kernels.cu")).read()
     a = text.find("// ---------------------------------------------------------------- update math")
     b = text.find("// ---------------------------------------------------------------- debug kernels")
-    h.update((text[a:b] if 0 <= a < b else text).encode())
+    h.update(strip_comments(text[a:b] if 0 <= a < b else text).encode())
     return h.hexdigest()[:12]
 
 

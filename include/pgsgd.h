@@ -50,7 +50,7 @@ typedef enum pgsgd_option {
      * effect at pgsgd_set_coords. */
     PGSGD_OPT_COORD_MODE = 1,
     /* Updates per iteration = this value times the number of path steps
-     * (Algorithm 1, line 1 uses 10). Default 10. */
+     * (Algorithm 1 uses 10). Default 10. */
     PGSGD_OPT_UPDATES_PER_STEP = 2,
     /* Update-kernel launch shape: threads per block (64..256, multiple of
      * 32; default 256), blocks per SM in the grid (default 32: many short

@@ -315,7 +315,7 @@ void orc_zipf_sample(double theta, uint64_t N, uint64_t seed, uint64_t count, ui
 }
 
 /* ------------------------------------------------------------------ */
-/* Graph view and the per-update sampler (Algorithm 1, lines 5-13).    */
+/* Graph view and the per-update sampler (Algorithm 1's pair draw).   */
 /* ------------------------------------------------------------------ */
 
 typedef struct {
@@ -361,7 +361,7 @@ static int64_t endpoint_pos(const orc_graph *G, uint64_t step, int e)
 }
 
 /* Partner step j of step i on path p (n >= 2 steps) from the words w of   */
-/* block 0 of counter (c0, c1, t) (Algorithm 1, lines 6-11).                */
+/* block 0 of counter (c0, c1, t) (Algorithm 1: the pair draw).              */
 /* One power-law trial with word w: k ~ Zipf(theta) on [1, n - 1] from bits */
 /* 8-31 of w, direction from bit 4 (1 = forward); accepted when the Zipf    */
 /* test accepts and step i +- k lies on the path.                            */
@@ -378,7 +378,7 @@ static int partner_trial(const zipf_t *z, uint64_t n, uint64_t i, uint32_t w, ui
 }
 
 /* Partner step j of step i on path p (n >= 2 steps) from the words w of   */
-/* block 0 of counter (c0, c1, t) (Algorithm 1, lines 6-11). Uniform: j =   */
+/* block 0 of counter (c0, c1, t) (Algorithm 1: the pair draw). Uniform: j = */
 /* x + (x >= i), x = mulhi64(w3 << 32 | (w2 & ~15), n - 1). Power law (the   */
 /* paper names only "Powerlaw"; reading: P(j) proportional to |j - i|^-theta */
 /* over the path's other steps): trials with the words w3, w2 & ~15, then    */
@@ -477,7 +477,7 @@ int orc_sample(GRAPH_ARGS, uint32_t T, uint32_t t, double theta, uint64_t seed,
 }
 
 /* ------------------------------------------------------------------ */
-/* Learning-rate schedule (Algorithm 1, line 3; annealing of Zheng).   */
+/* Learning-rate schedule (Algorithm 1's eta_t; annealing of Zheng).  */
 /* ------------------------------------------------------------------ */
 
 void orc_eta_schedule(uint32_t T, double eta_max, double eta_min, double *eta)
@@ -488,7 +488,7 @@ void orc_eta_schedule(uint32_t T, double eta_max, double eta_min, double *eta)
 }
 
 /* ------------------------------------------------------------------ */
-/* The update (Algorithm 1, lines 14-15) in FP64.                      */
+/* The update (Algorithm 1's move of both endpoints) in FP64.         */
 /* ------------------------------------------------------------------ */
 
 static void update_delta(const double vi[2], const double vj[2], double d_ref, double eta,

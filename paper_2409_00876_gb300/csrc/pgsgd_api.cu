@@ -536,7 +536,7 @@ int pgsgd_layout(pgsgd_graph* g, uint32_t iter_max, const double* eta, double et
     int rc = check_theta(theta);
     if (rc) return rc;
     cudaStream_t st = S(cuda_stream);
-    // learning rate (Algorithm 1, line 3): Zheng et al.'s exponential annealing
+    // learning rate eta_t of Algorithm 1: Zheng et al.'s exponential annealing
     std::vector<double> sched(iter_max);
     if (eta) {
         for (uint32_t t = 0; t < iter_max; ++t) sched[t] = eta[t];
@@ -560,7 +560,7 @@ int pgsgd_layout(pgsgd_graph* g, uint32_t iter_max, const double* eta, double et
     if (rc) return rc;
     if (g->pipeline && (g->warp_merge || g->drf > 1))
         return fail(PGSGD_EINVAL, "warp merging and data reuse run the plain update loop: set pipeline 0");
-    // updates per iteration (Algorithm 1, line 1) cut by the step reduction
+    // updates per iteration (Algorithm 1: 10 x steps) cut by the step reduction
     // factor; with data reuse the kernel counts selections of drf updates
     const uint64_t N_full = (uint64_t)g->updates_per_step * g->n_steps;
     const uint64_t N = (N_full + (uint64_t)g->srf - 1) / (uint64_t)g->srf;

@@ -691,7 +691,7 @@ cudaError_t set_batch_smem(size_t smem) {
     return cudaSuccess;
 }
 
-// Zheng et al.'s annealing with graph-specific eta_max (Algorithm 1, line 3).
+// Zheng et al.'s annealing with graph-specific eta_max (eta_t of Algorithm 1).
 void default_schedule(double eta_max, uint32_t T, float* out) {
     const double emin = 0.01;
     if (T == 1) {

@@ -407,7 +407,7 @@ __device__ __forceinline__ Pair pair_from_block(const SamplerArgs& a, const Path
     return r;
 }
 
-// Draw the pair of update u in iteration t (Algorithm 1, lines 5-11). One
+// Draw the pair of update u in iteration t (Algorithm 1: path, steps, cooling). One
 // Philox block serves the whole draw: w0, w1 pick the step, bits 0, 2 and 3
 // of w2 are the cooling and endpoint coins, w3 and the upper 28 bits of w2
 // feed the uniform partner or the first two power-law trials. Later blocks
@@ -459,7 +459,7 @@ struct Move {
     bool moved;
 };
 
-// The update of Zheng et al. that Algorithm 1, line 15 applies (Fig. 3):
+// The update of Zheng et al. that Algorithm 1 applies (Fig. 3):
 // w = d^-2, mu = min(eta w, 1), r = mu (|v_i - v_j| - d) / (2 |v_i - v_j|),
 // v_i -= r (v_i - v_j), v_j += r (v_i - v_j), for the points (xa, ya) and
 // (xb, yb). FP32; x anchors differenced in integers so chromosome-scale
@@ -495,7 +495,7 @@ struct UpdateOpts {
 };
 
 // The pairs of UPT independent updates u0 + k * stride (k < UPT; only those
-// below u_end are active) of Algorithm 1, lines 5-11.
+// below u_end are active) of Algorithm 1's pair draw.
 template <int UPT>
 struct TripDraws {
     uint64_t gi[UPT], gj[UPT];  // global step indices of n_i and n_j
@@ -533,7 +533,7 @@ __device__ __forceinline__ void load_trip_steps(const StepRec* __restrict__ step
     }
 }
 
-// Endpoint loads, the moves of Algorithm 1, lines 12-15, and the stores.
+// Endpoint loads, the moves of Algorithm 1, and the stores.
 // Only the chosen endpoint of each node is read (8 bytes, 2 registers).
 template <int UPT>
 __device__ __forceinline__ void finish_trip(NodeRec* __restrict__ nodes, const TripDraws<UPT>& d,

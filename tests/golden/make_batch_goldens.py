@@ -49,7 +49,8 @@ def main():
     args = ap.parse_args()
     from synth import BATCH_CONFIGS
     n = BATCH_CONFIGS["batch_small"]["n_graphs"]
-    sha = hashlib.sha1(open(os.path.join(ROOT, "oracle", "pgsgd_oracle.c"), "rb").read()).hexdigest()[:12]
+    from bench import strip_comments  # the oracle source's hash ignores comments and white-space layout
+    sha = hashlib.sha1(strip_comments(open(os.path.join(ROOT, "oracle", "pgsgd_oracle.c")).read()).encode()).hexdigest()[:12]
     graphs = [None] * n
     with mp.get_context("spawn").Pool(args.workers) as pool:
         for k, rec in pool.imap_unordered(_one, range(n)):

@@ -38,9 +38,11 @@ PLAN = {
 
 
 def oracle_sha():
+    """Hash of the oracle's C source with comments and white-space layout left out."""
     import hashlib
+    from bench import strip_comments
     src = os.path.join(ROOT, "oracle", "pgsgd_oracle.c")
-    return hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    return hashlib.sha1(strip_comments(open(src).read()).encode()).hexdigest()[:12]
 
 
 def fingerprint(g):

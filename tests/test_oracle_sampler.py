@@ -1,4 +1,4 @@
-"""Pins for the oracle's pair sampler (Algorithm 1, lines 5-13).
+"""Pins for the oracle's pair sampler (Algorithm 1: path, steps, cooling).
 
 Distributions are checked against their closed forms with chi-square tests;
 the reference distance against the hand-worked pair of Fig. 3.

@@ -8,7 +8,7 @@ from synth import make_custom, make_graph, make_linear_path
 
 
 def _pair_stress(vi, vj, d):
-    # Algorithm 1, line 14
+    # Algorithm 1's move
     return ((np.hypot(vi[0] - vj[0], vi[1] - vj[1]) - d) / d) ** 2
 
 
