@@ -66,6 +66,7 @@ def _L():
             lib.orc_exp_f32.restype = C.c_float
             lib.orc_zipf_consts.argtypes = [dbl, u64, P]
             lib.orc_zipf_sample.argtypes = [dbl, u64, u64, u64, P]
+            lib.orc_zipf_trials.argtypes = [dbl, u64, u32, u32, P]
             lib.orc_sample.argtypes = gargs + [u32, u32, dbl, u64, u64, u64, P]
             lib.orc_sample.restype = i32
             lib.orc_sample_wm.argtypes = gargs + [u32, u32, dbl, u64, i32, u64, u64, P]
@@ -153,6 +154,14 @@ def zipf_sample(theta: float, N: int, seed: int, count: int) -> np.ndarray:
     """count Zipf(theta) draws on [1, N] by the layout's rejection-inversion."""
     out = np.zeros(count, dtype=np.uint64)
     _L().orc_zipf_sample(float(theta), int(N), int(seed), int(count), _ptr(out))
+    return out
+
+
+def zipf_trials(theta: float, N: int, m_begin: int = 0, count: int = 1 << 24) -> np.ndarray:
+    """One rejection-inversion trial per word w = (m_begin + m) << 8: the k it
+    accepts, 0 where it rejects. m over [0, 2^24) covers every trial word."""
+    out = np.zeros(count, dtype=np.uint64)
+    _L().orc_zipf_trials(float(theta), int(N), int(m_begin), int(count), _ptr(out))
     return out
 
 

@@ -28,7 +28,8 @@
  *     its 95 % confidence interval mu +- 1.96 sigma / sqrt(n), sigma from a
  *     second pass over the same samples.
  *
- * Readings where the paper is silent (each one is listed in the design notes):
+ * Readings where the paper is silent (readings R2-R9 and R11 of the list of
+ * readings kept with the library's design):
  *   - Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key
  *     (seed_lo, seed_hi). Update u of iteration t uses counter
  *     (u_lo, u_hi, t, b) for block b = 0, 1, ...; words w0..w3 come from block
@@ -300,6 +301,19 @@ static uint64_t zipf_draw(const zipf_t *z, uint32_t first_word, uint64_t seed,
         if (zipf_trial(z, w[(m - 1) % 4], &k)) return k;
     }
     return 1;
+}
+
+/* Test helper: one Zipf(theta) trial on [1, N] for each trial word          */
+/* w = (m_begin + m) << 8, m in [0, count); out[m] = k when the trial        */
+/* accepts, 0 when it rejects. A trial reads bits 8-31 of its word only, so  */
+/* m over [0, 2^24) enumerates every behaviour of one trial.                  */
+void orc_zipf_trials(double theta, uint64_t N, uint32_t m_begin, uint32_t count, uint64_t *out)
+{
+    zipf_t z = zipf_setup(theta, N);
+    for (uint32_t m = 0; m < count; ++m) {
+        uint64_t k;
+        out[m] = zipf_trial(&z, (m_begin + m) << 8, &k) ? k : 0;
+    }
 }
 
 /* Test helper: count Zipf(theta) draws on [1, N] keyed by (q, 0x40000000);  */
