@@ -115,7 +115,7 @@ class ClockSampler:
 
     FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
               "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
-              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap", "timestamp"]
 
     def __init__(self, index):
         self.index = index
@@ -160,7 +160,7 @@ def summarize_clocks(lines):
     names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
     for ln in lines:
         parts = [p.strip() for p in ln.split(",")]
-        if len(parts) < len(ClockSampler.FIELDS):
+        if len(parts) < 8:  # the timestamp (field 9) is not needed here
             continue
         try:
             sm.append(float(parts[0]))
@@ -176,6 +176,37 @@ def summarize_clocks(lines):
     loaded = [s for s in sm if s >= 0.5 * top] or sm
     return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax),
             "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _sample_time(field):
+    """Epoch seconds of an nvidia-smi timestamp ("2026/12/04 06:12:34.567", local time)."""
+    from datetime import datetime
+    try:
+        return datetime.strptime(field.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+    except ValueError:
+        return None
+
+
+def clocks_in_windows(lines, windows):
+    """Median SM clock and power of the samples taken inside the host-time
+    windows [(t0, t1), ...] (epoch seconds): the clock a phase ran at."""
+    sm, pw = [], []
+    for ln in lines:
+        parts = [p.strip() for p in ln.split(",")]
+        if len(parts) < len(ClockSampler.FIELDS):
+            continue
+        t = _sample_time(parts[8])
+        if t is None or not any(a <= t <= b for a, b in windows):
+            continue
+        try:
+            sm.append(float(parts[0]))
+            pw.append(float(parts[2]))
+        except ValueError:
+            continue
+    if not sm:
+        return {"sm_mhz_median": None, "samples": 0}
+    return {"sm_mhz_median": statistics.median(sm), "sm_mhz_min": min(sm), "power_w_median": statistics.median(pw),
+            "samples": len(sm)}
 
 
 # ---------------------------------------------------------------- workload
@@ -201,26 +232,86 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def cpu_baseline(g, budget_s=12.0, warmup=False):
-    """The oracle (threaded Hogwild! mode, all host cores) on the first updates
-    of iteration 0 of the same workload, sized to take about budget_s."""
+def _oracle_rate(g, eta, t, budget_s, threads):
+    """Updates/s of the oracle's Hogwild! mode on the first updates of
+    iteration t, sized to take about budget_s (a probe sizes the sample)."""
     import oracle as O
-    threads = os.cpu_count() or 1
-    eta = O.eta_schedule(ITERS, O.default_eta_max(g))
     probe = max(100_000, min(g.n_steps, 2_000_000))
     t0 = time.perf_counter()
-    O.layout(g, g.init_xy, T=ITERS, eta=eta, theta=THETA, seed=SEED, t_end=1, n_updates=probe,
+    O.layout(g, g.init_xy, T=ITERS, eta=eta, theta=THETA, seed=SEED, t_begin=t, t_end=t + 1, n_updates=probe,
              n_threads=threads)
     rate = probe / max(time.perf_counter() - t0, 1e-6)
     n = int(min(max(rate * budget_s, probe), 10 * g.n_steps))
     t0 = time.perf_counter()
-    O.layout(g, g.init_xy, T=ITERS, eta=eta, theta=THETA, seed=SEED, t_end=1, n_updates=n,
+    O.layout(g, g.init_xy, T=ITERS, eta=eta, theta=THETA, seed=SEED, t_begin=t, t_end=t + 1, n_updates=n,
              n_threads=threads)
-    dt = time.perf_counter() - t0
+    return n, time.perf_counter() - t0
+
+
+def cpu_baseline(g, budget_s=12.0, warmup=False):
+    """The oracle (threaded Hogwild! mode, all host cores) on bounded samples
+    of the same workload: the first updates of a mixed iteration (t = 2: half
+    uniform, half power-law partners) and of a cooling iteration (t = 20: all
+    power-law partners, with their rejection trials), about budget_s / 2 each.
+    The rate is updates / time over both samples; a whole layout has 15
+    iterations of each kind, so this weights them as the layout does."""
+    import oracle as O
+    threads = os.cpu_count() or 1
+    eta = O.eta_schedule(ITERS, O.default_eta_max(g))
+    parts = {t: _oracle_rate(g, eta, t, budget_s / 2, threads) for t in (2, 20)}
+    n = sum(v[0] for v in parts.values())
+    dt = sum(v[1] for v in parts.values())
+    desc = ", ".join(f"t = {t}: first {v[0]} updates ({v[0] / (10 * g.n_steps):.2%} of the iteration) in "
+                     f"{v[1]:.1f} s = {v[0] / v[1]:.3g} upd/s" for t, v in parts.items())
     return {"value": n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"first {n} updates of iteration 0 of the same graph and seed "
-                      f"({n / (10 * g.n_steps):.3%} of one iteration), FP64, {threads} threads, "
-                      f"{dt:.1f} s"}
+            "per_iteration_kind": {"mixed_t2": parts[2][0] / parts[2][1], "cooling_t20": parts[20][0] / parts[20][1]},
+            "sample": f"bounded samples of the same graph and seed, FP64, {threads} threads: {desc}"}
+
+
+def cpu_full_layouts(names=("tiny",)):
+    """Whole oracle layouts (30 iterations x 10 x S updates) timed on the host:
+    one thread (the sequential definition) and all cores (Hogwild!)."""
+    import oracle as O
+    from synth import make_graph
+    threads = os.cpu_count() or 1
+    out = {}
+    for name in names:
+        g = make_graph(name)
+        eta = O.eta_schedule(ITERS, O.default_eta_max(g))
+        row = {"updates": ITERS * 10 * g.n_steps}
+        for k in sorted({1, threads}):
+            t0 = time.perf_counter()
+            O.layout(g, g.init_xy, T=ITERS, eta=eta, theta=THETA, seed=SEED, n_threads=k)
+            dt = time.perf_counter() - t0
+            row[f"threads_{k}"] = {"seconds": dt, "updates_per_s": row["updates"] / dt}
+        out[name] = row
+    return out
+
+
+def stress_vs_oracle(G, config):
+    """The layout's sampled stress (Eq. 2) against the oracle's layouts of the
+    same graph under the same layout seed, on the same sample set (the stored
+    record's samples per step and stress seed; tests/golden/oracle_layouts.json,
+    written by tests/golden/make_oracle_layouts.py)."""
+    path = os.path.join(ROOT, "tests", "golden", "oracle_layouts.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path)).get(config)
+    if not rec:
+        return None
+    runs = [r for r in rec["runs"] if r["seed"] == SEED]
+    if not runs:
+        return None
+    st = G.stress(rec["stress_samples_per_step"], seed=rec["stress_seed"])
+    ref = np.array([r["stress"] for r in runs])
+    out = {"samples_per_step": rec["stress_samples_per_step"], "stress_seed": rec["stress_seed"],
+           "layout_seed": SEED, "gpu_mean": st["mean"], "gpu_ci": [st["ci_lo"], st["ci_hi"]],
+           "oracle_mean": float(ref.mean()), "oracle_runs": len(ref), "oracle_threads": rec["oracle_threads"],
+           "oracle_ci_first_run": [runs[0]["ci_lo"], runs[0]["ci_hi"]],
+           "ratio": st["mean"] / float(ref.mean())}
+    if len(ref) > 1:
+        out["oracle_run_to_run_rel_sd"] = float(ref.std(ddof=1) / ref.mean())
+    return out
 
 
 # ---------------------------------------------------------------- reference arm
@@ -243,9 +334,12 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": updates_per_step / value * 1e3, "higher_is_better": True,
+        "ms_per_step_extrapolated": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.config], "name": args.config,
-                   "sample": "each step times a bounded sample of the layout (see cpu_baseline)"},
+                   "sample": "each step times bounded samples of a mixed (t = 2) and a cooling (t = 20) "
+                             "iteration (see cpu_baseline); ms_per_step is one whole layout's updates at "
+                             "that rate, extrapolated, not timed"},
         "cpu_baseline": cb,
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -273,10 +367,27 @@ def run_gpu(args):
     updates_per_step = ITERS * 10 * S
     stream = torch.cuda.current_stream()
 
-    def step(timing=False):
+    windows = {"layout": [], "stress": []}
+    phase_events = []
+
+    def step(timed=False):
+        t0 = time.time()
         G.set_coords(xy0)
         G.layout(ITERS, theta=THETA, seed=SEED)
-        return G.stress(STRESS_PER_STEP, seed=STRESS_SEED)
+        if timed:
+            # phase boundary: host time for the clock record, an event for the device time
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(stream)
+            stream.synchronize()
+            t1 = time.time()
+        st = G.stress(STRESS_PER_STEP, seed=STRESS_SEED)  # synchronous
+        if timed:
+            ev2 = torch.cuda.Event(enable_timing=True)
+            ev2.record(stream)
+            windows["layout"].append((t0, t1))
+            windows["stress"].append((t1, time.time()))
+            phase_events.append((ev, ev2))
+        return st
 
     for _ in range(args.warmup):
         step()
@@ -293,7 +404,7 @@ def run_gpu(args):
     e0.record(stream)
     st = None
     for _ in range(args.steps):
-        st = step()
+        st = step(timed=True)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -301,6 +412,18 @@ def run_gpu(args):
     ms = e0.elapsed_time(e1)
     upd_ms, launches, upd = G.timing_read(reset=True)
     G.set_option("timing", 0)
+    stress_ms = [a.elapsed_time(b) for a, b in phase_events]
+    n_samples = STRESS_PER_STEP * S
+    phases = {"layout": {"update_launch_ms_per_step": upd_ms / args.steps,
+                         **clocks_in_windows(clocks.lines, windows["layout"])},
+              "stress": {"ms_per_step": statistics.mean(stress_ms), "ms_each": [round(x, 1) for x in stress_ms],
+                         "samples_per_s": n_samples / (statistics.mean(stress_ms) / 1e3),
+                         **clocks_in_windows(clocks.lines, windows["stress"])}}
+    ph = phases["stress"]
+    if ph.get("sm_mhz_median"):
+        # time x clock: equal across GPUs when a difference in time is a difference in clock
+        ph["ms_x_ghz"] = ph["ms_per_step"] * ph["sm_mhz_median"] / 1e3
+    vs_oracle = stress_vs_oracle(G, args.config) if rank == 0 else None
     ms_max = max_over_ranks(ms, dev)
     value = aggregate_rate(updates_per_step * args.steps, ms, dev)
 
@@ -311,6 +434,7 @@ def run_gpu(args):
     per_launch_ms = upd_ms / max(launches, 1)
     updates_per_launch = upd / max(launches, 1)
     achieved = BYTES_PER_UPDATE * updates_per_launch / (per_launch_ms / 1e3) / 1e9
+    gather = hbm_gather(pg) if args.config in ("chrom", "prof") else None
     traffic = None
     tpath = os.path.join(ROOT, "profiles", f"update_kernel_traffic_{args.config}.json")
     if os.path.exists(tpath):
@@ -326,6 +450,7 @@ def run_gpu(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.skip_cpu:
         cpu = cpu_baseline(g, budget_s=args.cpu_budget)
+        cpu["full_layouts"] = cpu_full_layouts(tuple(args.cpu_full))
 
     forms = None
     if rank == 0 and not args.no_forms and args.config == "chrom":
@@ -346,8 +471,11 @@ def run_gpu(args):
             "stress": {"mean": st["mean"], "ci_lo": st["ci_lo"], "ci_hi": st["ci_hi"],
                        "n_valid": st["n_valid"]},
             "layout_only_updates_per_s": upd / (upd_ms / 1e3) if upd_ms > 0 else None,
-            "roofline": roofline_for(args.config, achieved, peak, peak_kind, traffic, per_launch_ms),
+            "stress_vs_oracle": vs_oracle,
+            "roofline": roofline_for(args.config, achieved, peak, peak_kind, traffic, per_launch_ms, gather,
+                                     2 * updates_per_launch / (per_launch_ms / 1e3)),
             "clocks": clk,
+            "phases": phases,
             "gpu_launches": gpu_launches,
             "e2e": e2e,
             "cpu_baseline": cpu,
@@ -391,7 +519,10 @@ def batch_form(dev, full=False, log=None, name="batch256"):
     def stress_summary():
         st = B.stress(STRESS_PER_STEP, seed=STRESS_SEED)
         m = np.array([r["mean"] for r in st])
-        return {"mean_over_graphs": float(m.mean()), "median": float(np.median(m)), "max": float(m.max())}
+        out = {"mean_over_graphs": float(m.mean()), "median": float(np.median(m)), "max": float(m.max())}
+        if name == "batch256":
+            out["vs_oracle"] = batch_subset_vs_oracle(m)
+        return out
 
     _batch_timed(B, xy, seeds)  # warm: the tuned shape's CUDA graph
     ms, launches, _ = _batch_timed(B, xy, seeds)
@@ -402,9 +533,10 @@ def batch_form(dev, full=False, log=None, name="batch256"):
            "autotune_keys": "mode/pipeline/updates_per_thread/block/chunk",
            "batched": {"ms": ms, "updates_per_s": updates / (ms / 1e3), "launches": launches,
                        "stress": stress_summary()}}
-    others = [("per_graph_launches", dict(mode=2, cuda_graph=0))]
+    # the persistent kernel (one launch per layout) is reported beside the tuned choice every time
+    others = [("persistent", dict(mode=1)), ("per_graph_launches", dict(mode=2, cuda_graph=0))]
     if full:
-        others = [("launch_per_iteration", dict(mode=0, cuda_graph=1)), ("persistent", dict(mode=1)),
+        others = [("launch_per_iteration", dict(mode=0, cuda_graph=1)),
                   ("per_graph_launches_cuda_graph", dict(mode=2, cuda_graph=1))] + others
     for name, opts in others:
         for k, v in opts.items():
@@ -434,6 +566,25 @@ def batch_form(dev, full=False, log=None, name="batch256"):
     return out
 
 
+def batch_subset_vs_oracle(per_graph):
+    """Per-graph stress of a batch256 layout against the oracle's layouts of
+    a fixed 16-graph subset (same graph, same layout seed, same samples:
+    tests/golden/oracle_batch256_subset.json, written by
+    tests/golden/make_batch_goldens.py). The geometric mean of the ratios,
+    with a CI95 from their graph-to-graph spread."""
+    path = os.path.join(ROOT, "tests", "golden", "oracle_batch256_subset.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    idx = [g["index"] for g in rec["graphs"]]
+    ratios = np.array([per_graph[k] / g["stress"][0] for k, g in zip(idx, rec["graphs"])])
+    lr = np.log(ratios)
+    half = 1.96 * lr.std(ddof=1) / np.sqrt(len(lr))
+    return {"graphs": len(idx), "indices": idx, "n_steps": [g["n_steps"] for g in rec["graphs"]],
+            "ratios": [round(float(r), 4) for r in ratios], "geomean_ratio": float(np.exp(lr.mean())),
+            "geomean_ci95": [float(np.exp(lr.mean() - half)), float(np.exp(lr.mean() + half))]}
+
+
 def dstress_form(dev, n_pairs=10_000_000, steps=200):
     """Differentiable sampled stress on the laid-out 200 k-node graph: forward
     and backward kernel times for 10 M pairs, and a 200-step full-batch
@@ -460,20 +611,37 @@ def dstress_form(dev, n_pairs=10_000_000, steps=200):
         if i:
             fw.append(t1 - t0)
             bw.append(t2 - t1)
-    before = G.stress(STRESS_PER_STEP, seed=STRESS_SEED)["mean"]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    xr, trace = refine(G, xy, steps=steps, lr=0.05, n_pairs=n_pairs, seed=9)
-    torch.cuda.synchronize()
-    ref_s = time.perf_counter() - t0
-    G.set_coords(xr)
-    after = G.stress(STRESS_PER_STEP, seed=STRESS_SEED)["mean"]
-    return {"workload": WORKLOADS["mid"] + ", after a 30-iteration PG-SGD layout", "pairs": n_pairs,
-            "forward_ms": 1e3 * min(fw), "backward_ms": 1e3 * min(bw),
-            "pairs_per_s_backward": n_pairs / min(bw),
-            "refine_steps": steps, "refine_s": ref_s, "objective_first": trace[0], "objective_last": trace[-1],
-            "stress_before": before, "stress_after": after, "stress_change": after - before,
-            "timing": "host wall clock around synchronous calls (forward includes its readback)"}
+    held_out = list(range(100, 108))  # stress seeds the refinement never sees
+
+    def held(x):
+        G.set_coords(x)
+        return np.array([G.stress(STRESS_PER_STEP, seed=sd)["mean"] for sd in held_out])
+
+    before = held(xy)
+    out = {"workload": WORKLOADS["mid"] + ", after a 30-iteration PG-SGD layout", "pairs": n_pairs,
+           "forward_ms": 1e3 * min(fw), "backward_ms": 1e3 * min(bw), "pairs_per_s_backward": n_pairs / min(bw),
+           "refine_steps": steps, "stress_before": float(before.mean()),
+           "held_out": f"Eq. 2 at {STRESS_PER_STEP} samples per step under stress seeds {held_out[0]}-{held_out[-1]}; "
+                       "change = mean over seeds of (after - before) on the same samples, CI95 over the seeds",
+           "timing": "host wall clock around synchronous calls (forward includes its readback)"}
+    for name, resample in (("full_batch", False), ("resampled", True)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xr, trace = refine(G, xy, steps=steps, lr=0.05, n_pairs=n_pairs, seed=9, resample=resample)
+        torch.cuda.synchronize()
+        ref_s = time.perf_counter() - t0
+        d = held(xr) - before
+        half = 1.96 * d.std(ddof=1) / np.sqrt(len(d))
+        out[name] = {"refine_s": ref_s, "objective_first": trace[0], "objective_last": trace[-1],
+                     "stress_after": float((before + d).mean()), "stress_change": float(d.mean()),
+                     "stress_change_ci95": [float(d.mean() - half), float(d.mean() + half)],
+                     "relative_change": float(d.mean() / before.mean()),
+                     "significant": bool(abs(d.mean()) > half)}
+    # the full-batch figures under their earlier names
+    out.update(refine_s=out["full_batch"]["refine_s"], objective_first=out["full_batch"]["objective_first"],
+               objective_last=out["full_batch"]["objective_last"], stress_after=out["full_batch"]["stress_after"],
+               stress_change=out["full_batch"]["stress_change"])
+    return out
 
 
 def reuse_form(G, xy0, schemes=((1, 1, 1), (2, 2, 0), (4, 4, 0), (8, 8, 0))):
@@ -568,7 +736,8 @@ def run_batch(args):
                        "updates_per_step": updates_per_step, "tuned": tuned,
                        "l2": f"inputs larger than L2 ({16 * S / 1e9:.1f} GB of step records), no flush",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
-            "stress": {"mean_over_graphs": float(m.mean()), "max": float(m.max())},
+            "stress": {"mean_over_graphs": float(m.mean()), "max": float(m.max()),
+                       "vs_oracle": batch_subset_vs_oracle(m) if args.config == "batch256" else None},
             "layout_only_updates_per_s": upd / (lay_ms / 1e3),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "kernel": "batch layout kernels",
@@ -581,12 +750,35 @@ def run_batch(args):
     return 0
 
 
-def roofline_for(config, achieved, peak, peak_kind, traffic, launch_ms):
+def hbm_gather(pg):
+    """Random-read ceilings of HBM measured in-repo (pgsgd_hbm_gather_bandwidth,
+    4 GiB buffer): reads/s of the update kernel's step-record form (16 bytes,
+    64-byte prefetch hint), of the same read without the hint and of whole
+    random 64-byte blocks; best of 4 and 8 resident blocks per SM."""
+    best = {m: max(pg.hbm_gather_rate(4 << 30, 4, m, b) for b in (4, 8)) for m in (0, 1, 2)}
+    return {"reads_per_s_16B_hint64": best[0], "reads_per_s_16B_nohint": best[1],
+            "reads_per_s_64B_block": best[2],
+            "gbs_16B_hint64_as_32B_sectors": best[0] * 32 / 1e9, "gbs_16B_hint64_as_64B_accesses": best[0] * 64 / 1e9,
+            "gbs_64B_block": best[2] * 64 / 1e9}
+
+
+def roofline_for(config, achieved, peak, peak_kind, traffic, launch_ms, gather=None, step_reads_per_s=None):
     """HBM roofline; for graphs whose records fit in L2 (mid, tiny) the bound is
-    L2, against the L2 read bandwidth measured in-repo (pgsgd_l2_bandwidth)."""
+    L2, against the L2 read bandwidth measured in-repo (pgsgd_l2_bandwidth).
+    With `gather` (hbm_gather) the update kernel's random step-record reads
+    per second are also set against the measured random-read ceiling of the
+    same read form: random_gather_gbs counts each read as its 32-byte sector,
+    the unit of the 192-byte model."""
     r = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
          "traffic": traffic, "kernel": "update_kernel", "bytes_per_update_model": BYTES_PER_UPDATE,
          "peak_kind": peak_kind, "launch_ms": launch_ms}
+    if gather:
+        r["random_gather_gbs"] = gather["gbs_16B_hint64_as_32B_sectors"]
+        r["frac_of_random_gather"] = achieved / r["random_gather_gbs"]
+        r["random_gather"] = gather
+        if step_reads_per_s:
+            r["step_reads_per_s"] = step_reads_per_s
+            r["step_read_frac_of_random_read_rate"] = step_reads_per_s / gather["reads_per_s_16B_hint64"]
     if config in ("mid", "tiny"):
         import paper_2409_00876_gb300 as pg
         stream = max(pg.l2_bandwidth(mib << 20, 20, 0) for mib in (16, 32, 64))
@@ -697,6 +889,8 @@ def main(argv=None):
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-budget", type=float, default=10.0)
+    ap.add_argument("--cpu-full", nargs="*", default=["tiny"], choices=["tiny", "mid"],
+                    help="workloads whose whole oracle layout is timed on the host (1 thread and all cores)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the data-reuse, batched and differentiable forms (chromosome run) or the "
                          "schedule comparison (batch runs)")

@@ -320,8 +320,8 @@ int pgsgd_dstress_backward(pgsgd_graph *g, uint64_t n_pairs, uint64_t seed, doub
                            float *grad, void *cuda_stream);
 
 /*
- * Gradient of the single-pair stress ((|v_i - v_j| - d) / d)^2 (Algorithm 1,
- * line 14) of every update u in [u_begin, u_begin + count) of iteration t,
+ * Gradient of the single-pair stress ((|v_i - v_j| - d) / d)^2 (Algorithm 1's
+ * pair stress) of every update u in [u_begin, u_begin + count) of iteration t,
  * at the current layout: out[count][4] float32 (host) =
  * (d/dx_i, d/dy_i, d/dx_j, d/dy_j); zeros where the update is skipped.
  * Together with pgsgd_debug_sweep it shows each move equals
@@ -359,9 +359,11 @@ int pgsgd_timing_read(pgsgd_graph *g, double *total_ms, uint64_t *launches,
  * Scratch: a fixed file-scope device array of 96 KiB that every GPU which
  * loads the library holds until the process exits; it has room for the
  * partial sums of 4096 blocks (the grid is capped there). Limit:
- * n_paths <= 8192 (PGSGD_ERANGE beyond, with a message). The first call on a
- * device looks up the array's device address and sets the kernel's shared
- * memory limit, so make that first call before any stream capture. All calls
+ * n_paths <= 8192 (PGSGD_ERANGE beyond, with a message). Every call looks
+ * up the array's device address on the current device (cudaGetSymbolAddress)
+ * and sets the kernel's shared-memory limit, so it stays valid after
+ * cudaDeviceReset; the first call on a device may also load the library's
+ * kernels, so make that first call before any stream capture. All calls
  * share the array (each call writes every slot it reads, so nothing is
  * cleared): calls that overlap on the GPU, on any streams, race on it.
  */
@@ -382,6 +384,26 @@ int pgsgd_stress_noalloc(const uint32_t *node_len, uint32_t n_nodes,
  * frees everything it allocated.
  */
 int pgsgd_l2_bandwidth(uint64_t bytes, uint32_t reps, int mode, double *gbs, void *cuda_stream);
+
+/*
+ * Measurement helper, no counterpart in the paper: the rate of random reads
+ * from HBM (*loads_per_s, host: reads completed per second), the ceiling of a
+ * kernel bound by random record reads, as the update kernel is on graphs
+ * whose 16-byte step records are far larger than L2 (the memory-bound
+ * random access of Section III-B). Allocates a `bytes` buffer (1..64 GiB,
+ * keep it several times the L2 size), then times `reps` (1..100) launches of
+ * blocks_per_sm (1..8) 256-thread blocks per SM, 512 random reads per thread,
+ * four in flight. mode 0 = a 16-byte load with the evict-first policy and the
+ * 64-byte L2 prefetch-size hint (the form of the update kernel's step-record
+ * read); 1 = the same load without the hint; 2 = a random 64-byte block read
+ * as four coalesced 16-byte pieces by four lanes (one read = one block).
+ * Multiply by 32 (the sector a 16-byte read touches) or 64 (the DRAM access
+ * it costs with the hint) for GB/s. Synchronous; frees everything it
+ * allocated. PGSGD_EINVAL for arguments out of range, PGSGD_ENOMEM when the
+ * buffer cannot be allocated.
+ */
+int pgsgd_hbm_gather_bandwidth(uint64_t bytes, uint32_t reps, int mode, int blocks_per_sm,
+                               double *loads_per_s, void *cuda_stream);
 
 /* Message of the calling thread's last failure ("" if none). */
 const char *pgsgd_last_error(void);

@@ -15,7 +15,8 @@ import numpy as np
 from . import _native as N
 from ._native import PgsgdError, StressResult
 
-__all__ = ["Graph", "PgsgdError", "StressResult", "SAMPLE_DTYPE", "load_library", "l2_bandwidth"]
+__all__ = ["Graph", "PgsgdError", "StressResult", "SAMPLE_DTYPE", "load_library", "l2_bandwidth",
+           "hbm_gather_rate"]
 
 SAMPLE_DTYPE = np.dtype([("g", "<u8"), ("i", "<u8"), ("j", "<u8"), ("d_ref", "<i8"),
                          ("path", "<u4"), ("cooling", "u1"), ("e_i", "u1"),
@@ -31,6 +32,16 @@ def l2_bandwidth(bytes_=64 << 20, reps=20, mode=0, stream=None):
     lib = N.load()
     out = C.c_double()
     N.check(lib.pgsgd_l2_bandwidth(int(bytes_), int(reps), int(mode), C.byref(out), stream or _current_stream()))
+    return out.value
+
+
+def hbm_gather_rate(bytes_=4 << 30, reps=4, mode=0, blocks_per_sm=8, stream=None):
+    """Random reads per second from an HBM buffer of bytes_ (mode 0: 16-byte
+    loads with the 64-byte prefetch hint, 1: without it, 2: 64-byte blocks)."""
+    lib = N.load()
+    out = C.c_double()
+    N.check(lib.pgsgd_hbm_gather_bandwidth(int(bytes_), int(reps), int(mode), int(blocks_per_sm), C.byref(out),
+                                           stream or _current_stream()))
     return out.value
 
 

@@ -1,7 +1,7 @@
 // Device-side building blocks of the PG-SGD path: the packed records, the
 // Philox4x32-10 generator, binary32 elementary functions with a fixed
 // operation order, the Zipf rejection-inversion sampler and the per-update
-// pair draw of Algorithm 1 (Section II-C, lines 5-13).
+// pair draw of Algorithm 1 (Section II-C: path, steps, cooling and coins).
 //
 // Every floating-point operation that decides an integer (the Zipf draw) is
 // written with explicit round-to-nearest intrinsics (__fadd_rn, __fmul_rn,
@@ -359,8 +359,8 @@ __device__ __forceinline__ bool partner_trial(const ZipfConsts& zc, const float*
     return false;
 }
 
-// Partner step j of step i in a path of n >= 2 steps (Algorithm 1, lines
-// 6-11) from the words w2, w3 of block 0 of the update's counter (c0, c1, t).
+// Partner step j of step i in a path of n >= 2 steps (Algorithm 1's
+// partner draw) from the words w2, w3 of block 0 of the update's counter (c0, c1, t).
 // Uniform: j = x + (x >= i), x = mulhi64(w3 << 32 | (w2 & ~15), n - 1).
 // Power law: P(j) proportional to |j - i|^-theta over the path's other
 // steps: trials with the words w3, w2 & ~15, then blocks 1, 2, ... of the

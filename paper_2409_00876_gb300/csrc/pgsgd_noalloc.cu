@@ -7,8 +7,6 @@
 // and every call on a device shares it: calls whose work overlaps on the GPU
 // race on it. Each call's blocks write every slot its final reduction reads,
 // so nothing has to be cleared between calls.
-#include <mutex>
-
 #include "../../include/pgsgd.h"
 #include "pgsgd_internal.h"
 
@@ -18,16 +16,15 @@ namespace {
 constexpr int kNoAllocBlocks = 4096;               // partial-sum slots
 constexpr uint32_t kNoAllocMaxPaths = 8192;        // path and sample tables in shared memory
 constexpr int kNoAllocSlots = 3 * kNoAllocBlocks + 2;  // + sample count of the call
-constexpr int kMaxDevices = 64;
 
 // Scratch: [block][3] = (sum of terms, sum of squared terms, valid samples),
 // then the call's total number of samples at [3 * kNoAllocBlocks].
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocSlots];
 
 // In host code g_noalloc_scratch names a host-side shadow, not device memory:
-// its device address is looked up once per device and cached here.
-std::mutex g_mu;
-double* g_scratch_ptr[kMaxDevices] = {};
+// every call looks up its device address on the current device. Nothing is
+// cached, so a call stays valid after cudaDeviceReset or on a new primary
+// context, where the module (and the array) may load at another address.
 
 __global__ void stress_noalloc_kernel(const uint32_t* __restrict__ node_len,
                                       const uint64_t* __restrict__ path_off, uint32_t P,
@@ -182,31 +179,20 @@ extern "C" int pgsgd_stress_noalloc(const uint32_t* node_len, uint32_t n_nodes, 
                             "shared memory)", n_paths, kNoAllocMaxPaths);
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess && (dev < 0 || dev >= kMaxDevices))
-        return report_error(PGSGD_ERANGE, "pgsgd_stress_noalloc: device ordinal %d >= %d", dev, kMaxDevices);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess)
         return report_error(PGSGD_ECUDA, "pgsgd_stress_noalloc: device query: %s", cudaGetErrorString(e));
-    double* scratch = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_scratch_ptr[dev]) {
-            // once per device, with that device current: the array's device address
-            void* p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-            if (e != cudaSuccess || !p)
-                return report_error(PGSGD_ECUDA, "pgsgd_stress_noalloc: cudaGetSymbolAddress: %s",
-                                    cudaGetErrorString(e));
-            const size_t max_smem = 2 * (size_t)(kNoAllocMaxPaths + 1) * sizeof(uint64_t);
-            e = cudaFuncSetAttribute(stress_noalloc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)max_smem);
-            if (e != cudaSuccess)
-                return report_error(PGSGD_ECUDA, "pgsgd_stress_noalloc: shared memory attribute: %s",
-                                    cudaGetErrorString(e));
-            g_scratch_ptr[dev] = static_cast<double*>(p);
-        }
-        scratch = g_scratch_ptr[dev];
-    }
+    // with the caller's device current: the array's device address on it, and
+    // the kernel's shared-memory limit (host calls that allocate nothing)
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        return report_error(PGSGD_ECUDA, "pgsgd_stress_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    double* scratch = static_cast<double*>(p);
+    const size_t max_smem = 2 * (size_t)(kNoAllocMaxPaths + 1) * sizeof(uint64_t);
+    e = cudaFuncSetAttribute(stress_noalloc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+    if (e != cudaSuccess)
+        return report_error(PGSGD_ECUDA, "pgsgd_stress_noalloc: shared memory attribute: %s", cudaGetErrorString(e));
     int grid = sms * 8;
     if (grid > kNoAllocBlocks) grid = kNoAllocBlocks;  // never more partials than the array holds
     if (grid < 1) grid = 1;

@@ -1,14 +1,20 @@
-"""Write tests/golden/oracle_batch_small.json: the CPU oracle's layout quality
-on every graph of the small batch workload (12 graphs, 1 k - 12 k nodes,
-4 - 12 paths).
+"""Write the CPU oracle's per-graph layout quality for the batch workloads:
 
-For each graph and layout seed this runs Algorithm 1 in the oracle (FP64,
-one thread: the sequential reading of the method) from the generator's
-initial layout and records the sampled path stress (Eq. 2) of the result
-under a fixed stress seed. Only the oracle and the input generator are
-called; graphs run in parallel worker processes.
+- tests/golden/oracle_batch_small.json: every graph of the small batch
+  workload (12 graphs, 1 k - 12 k nodes, 4 - 12 paths), layout seeds 1-3,
+  one thread (the sequential reading of the method);
+- tests/golden/oracle_batch256_subset.json: a fixed subset of 16 graphs of
+  the 256-subgraph workload spanning its size range (the graphs at 16 evenly
+  spaced ranks 0..240 of 256 by size), each under the layout
+  seed the batch gives it (graph index + 1); one thread below 1 M steps,
+  Hogwild! threads above.
 
-    python tests/golden/make_batch_goldens.py [--workers 4]
+For each graph and layout seed this runs Algorithm 1 in the oracle (FP64)
+from the generator's initial layout and records the sampled path stress
+(Eq. 2) of the result under a fixed stress seed. Only the oracle and the
+input generator are called; graphs run in parallel worker processes.
+
+    python tests/golden/make_batch_goldens.py [--workload batch_small|batch256] [--workers 4]
 """
 import argparse
 import hashlib
@@ -18,47 +24,81 @@ import os
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 sys.path.insert(0, ROOT)
 
-OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_batch_small.json")
-SEEDS = [1, 2, 3]
+HERE = os.path.dirname(os.path.abspath(__file__))
 T = 30
 THETA = 0.99
 PER_STEP = 100
 STRESS_SEED = 7
+SMALL_SEEDS = [1, 2, 3]
+SUBSET_SIZE = 16
+SUBSET_TOP_RANK = 240       # ranks 0..240 of 256 by step count: the largest graphs stay out (CPU time)
+THREADED_ABOVE = 1_000_000  # steps; larger subset graphs use Hogwild! threads
 
 
-def _one(k):
+def subset_indices():
+    """Graph indices of the batch256 subset: 16 evenly spaced ranks (0 to 240)
+    of the graphs ordered by node count x path count (the size of their path
+    data), from the batch's shape table alone."""
+    from synth import BATCH_CONFIGS, batch_shapes
+    cfg = BATCH_CONFIGS["batch256"]
+    shapes = batch_shapes(cfg["n_graphs"], cfg["nodes"], cfg["paths"], cfg["seed"])
+    size = np.array([v * p for v, p, _ in shapes], dtype=np.float64)
+    order = np.argsort(size, kind="stable")
+    return [int(order[int(round(q))]) for q in np.linspace(0, SUBSET_TOP_RANK, SUBSET_SIZE)]
+
+
+def _one(job):
     import oracle as O
     from synth import make_batch
-    g = make_batch("batch_small")[k]
+    workload, k, seeds, threads = job
+    g = make_batch(workload, indices=[k])[0]
+    if threads is None:
+        threads = 1 if g.n_steps <= THREADED_ABOVE else max(1, (os.cpu_count() or 2) // 2)
     t0 = time.time()
     init = O.sampled_stress(g, g.init_xy, per_step=PER_STEP, seed=STRESS_SEED)["mean"]
     runs = []
-    for s in SEEDS:
-        xy, _ = O.layout(g, g.init_xy, T=T, theta=THETA, seed=s, n_threads=1)
+    for s in seeds:
+        xy, _ = O.layout(g, g.init_xy, T=T, theta=THETA, seed=s, n_threads=threads)
         runs.append(O.sampled_stress(g, xy, per_step=PER_STEP, seed=STRESS_SEED)["mean"])
-    return k, dict(n_nodes=g.n_nodes, n_paths=g.n_paths, n_steps=g.n_steps, init_stress=init, stress=runs,
-                   seconds=round(time.time() - t0, 1))
+    return k, dict(index=k, n_nodes=g.n_nodes, n_paths=g.n_paths, n_steps=g.n_steps, init_stress=init,
+                   seeds=seeds, stress=runs, oracle_threads=threads, seconds=round(time.time() - t0, 1))
 
 
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="batch_small", choices=["batch_small", "batch256"])
     ap.add_argument("--workers", type=int, default=4)
     args = ap.parse_args()
     from synth import BATCH_CONFIGS
-    n = BATCH_CONFIGS["batch_small"]["n_graphs"]
     from bench import strip_comments  # the oracle source's hash ignores comments and white-space layout
     sha = hashlib.sha1(strip_comments(open(os.path.join(ROOT, "oracle", "pgsgd_oracle.c")).read()).encode()).hexdigest()[:12]
-    graphs = [None] * n
+    if args.workload == "batch_small":
+        idx = list(range(BATCH_CONFIGS["batch_small"]["n_graphs"]))
+        jobs = [("batch_small", k, SMALL_SEEDS, 1) for k in idx]
+        out = os.path.join(HERE, "oracle_batch_small.json")
+    else:
+        idx = subset_indices()
+        jobs = [("batch256", k, [k + 1], None) for k in idx]
+        out = os.path.join(HERE, "oracle_batch256_subset.json")
+    recs = {}
     with mp.get_context("spawn").Pool(args.workers) as pool:
-        for k, rec in pool.imap_unordered(_one, range(n)):
-            graphs[k] = rec
+        for k, rec in pool.imap_unordered(_one, jobs):
+            recs[k] = rec
             print(k, rec, flush=True)
-    data = dict(workload="batch_small", oracle_sha=sha, iterations=T, theta=THETA, updates_per_step=10,
-                seeds=SEEDS, stress_samples_per_step=PER_STEP, stress_seed=STRESS_SEED, graphs=graphs)
-    with open(OUT, "w") as f:
+    graphs = [recs[k] for k in idx]
+    data = dict(workload=args.workload, oracle_sha=sha, iterations=T, theta=THETA, updates_per_step=10,
+                stress_samples_per_step=PER_STEP, stress_seed=STRESS_SEED, graphs=graphs)
+    if args.workload == "batch_small":
+        data["seeds"] = SMALL_SEEDS
+        for g in graphs:  # the small record keeps its original per-graph fields
+            for f in ("index", "seeds", "oracle_threads"):
+                g.pop(f)
+    with open(out, "w") as f:
         json.dump(data, f, indent=1)
 
 

@@ -112,3 +112,16 @@ def test_autograd_gradient_and_refinement_lower_stress(laid_out):
     # the optimised objective falls; the held-out Eq. 2 stress must not degrade
     assert trace[-1] < trace[0]
     assert after < 1.02 * before
+
+
+def test_autograd_leaves_the_graphs_layout_unchanged(laid_out):
+    """forward and backward differentiate the layout passed in; the layout the
+    graph holds (here the initial one) is the same afterwards, bit for bit."""
+    import torch
+    from paper_2409_00876_gb300.autograd import sampled_stress
+    pg, g, G, xy = laid_out
+    G.set_coords(g.init_xy)
+    held = G.get_coords()
+    x = torch.from_numpy(xy).cuda().requires_grad_(True)
+    sampled_stress(x, G, 100_000, 5).backward()
+    np.testing.assert_array_equal(G.get_coords(), held)

@@ -1,4 +1,4 @@
-"""The in-repo L2 bandwidth probe that sets the roofline of L2-resident graphs."""
+"""The in-repo L2 and HBM random-read probes that set the rooflines of the update kernel."""
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -11,3 +11,14 @@ def test_l2_bandwidth_is_plausible():
     # above any HBM3e figure and below an absurd bound; random sectors cost more than streaming
     assert 5_000 < stream < 200_000, stream
     assert 500 < rand < stream * 1.5, (rand, stream)
+
+
+def test_hbm_random_read_rate_is_plausible():
+    import paper_2409_00876_gb300 as pg
+    hint = pg.hbm_gather_rate(4 << 30, 2, 0)
+    plain = pg.hbm_gather_rate(4 << 30, 2, 1)
+    block = pg.hbm_gather_rate(4 << 30, 2, 2)
+    # every read costs at least one 32-byte sector of DRAM traffic, which cannot exceed
+    # ~1.5x the copy peak; and a random read rate below 1e9/s would mean a broken probe
+    for r in (hint, plain, block):
+        assert 1e9 < r < 1.5 * 8e12 / 32, (hint, plain, block)

@@ -1,5 +1,6 @@
-"""Pins for the oracle's update rule, schedule and layout loop (Algorithm 1,
-lines 3 and 14-15, with the update of Zheng et al. that Fig. 3 illustrates)."""
+"""Pins for the oracle's update rule, schedule and layout loop (Algorithm 1:
+the learning rate per iteration and the pair update, with the update of Zheng
+et al. that Fig. 3 illustrates)."""
 import numpy as np
 import pytest
 

@@ -1,13 +1,16 @@
 """pgsgd_stress_noalloc: the sampled path stress for callers that cannot
 allocate device memory (their memory belongs to another allocator or a fixed
 budget, or they must not allocate where they call). It must give what
-pgsgd_stress gives for the same layout and seed, call after call, although
-every call reuses one static scratch array. Collected last on purpose."""
+pgsgd_stress gives for the same layout and seed, and what the FP64 oracle
+computes on the same layout (Eq. 2), call after call, although every call
+reuses one static scratch array; and it must allocate no device memory.
+Collected last on purpose."""
 import ctypes as C
 
 import numpy as np
 import pytest
 
+import oracle as O
 from synth import make_graph
 
 pytestmark = pytest.mark.gpu
@@ -55,6 +58,49 @@ def test_noalloc_stress_matches_pgsgd_stress_on_two_calls_in_a_row(name):
         assert abs(got["mean"] - ref["mean"]) <= 1e-4 * ref["mean"]
         assert abs(got["std"] - ref["std"]) <= 1e-3 * ref["std"]
         assert got["ci_lo"] <= got["mean"] <= got["ci_hi"]
+
+
+def test_noalloc_stress_matches_the_oracle_and_allocates_nothing():
+    """Against the oracle's Eq. 2 on the same layout and samples (n_valid
+    exact, mean within 1e-4), and with the device's free memory and torch's
+    allocator statistics unchanged across a call after a warm-up call
+    (the device's free memory does not shrink)."""
+    import torch
+    import paper_2409_00876_gb300 as pg
+    from paper_2409_00876_gb300 import _native as N
+    lib = N.load()
+    g = make_graph("tiny")
+    G = pg.Graph.from_synth(g)
+    G.set_coords(g.init_xy)
+    G.layout(30, theta=0.99, seed=2)
+    xy = G.get_coords()
+    G.close()
+    dev = {k: torch.from_numpy(np.ascontiguousarray(getattr(g, k))).cuda()
+           for k in ("node_len", "path_off", "step_node", "step_rev", "step_pos")}
+    xy_dev = torch.from_numpy(xy).cuda()
+    for seed in (5, 6):
+        got = _noalloc(lib, dev, xy_dev, 100, seed)
+        ref = O.sampled_stress(g, xy, per_step=100, seed=seed)
+        assert int(got["n_valid"]) == ref["n_valid"]
+        assert abs(got["mean"] - ref["mean"]) <= 1e-4 * ref["mean"], (got, ref)
+    out = torch.zeros(RESULT.itemsize, dtype=torch.uint8, device="cuda")
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    args = (_ptr(dev["node_len"]), dev["node_len"].numel(), _ptr(dev["path_off"]), dev["path_off"].numel() - 1,
+            _ptr(dev["step_node"]), _ptr(dev["step_rev"]), _ptr(dev["step_pos"]), _ptr(xy_dev), 100, 7,
+            _ptr(out), stream)
+    assert lib.pgsgd_stress_noalloc(*args) == 0  # warm-up call
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    stats0 = torch.cuda.memory_stats()
+    assert lib.pgsgd_stress_noalloc(*args) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    stats1 = torch.cuda.memory_stats()
+    # a device allocation takes whole pages from the free memory; a stream-ordered
+    # pool that other code releases meanwhile can only raise it
+    assert free1 >= free0, (free0, free1)
+    for k in ("allocation.all.allocated", "reserved_bytes.all.current", "num_alloc_retries"):
+        assert stats1.get(k) == stats0.get(k), k
 
 
 def test_noalloc_rejects_too_many_paths_with_a_message():
