@@ -132,7 +132,21 @@ typedef enum pgsgd_option {
      * ceil(updates_per_step x S / SRF) selections (or updates, with DRF 1).
      * Both need PGSGD_OPT_PIPELINE = 0. */
     PGSGD_OPT_DRF = 17,
-    PGSGD_OPT_SRF = 18
+    PGSGD_OPT_SRF = 18,
+    /* Asynchronous step-record reads: 0 = off (default); D in {2, 3, 4, 6, 8}
+     * = every thread keeps the step-record reads of its next D updates in
+     * flight, copied into shared memory with cp.async, so outstanding reads
+     * cost no registers (one update per thread; compiled for min blocks 4,
+     * and 3 or 5 at D = 4). Same draws and moves as the plain loop. Ignored
+     * under warp merging and data reuse. */
+    PGSGD_OPT_ASYNC_DEPTH = 19,
+    /* The same for the sampled-stress kernel (pgsgd_stress): 0 = off
+     * (default), D in {2, 4, 8} samples' step-record reads in flight per
+     * thread. Same samples and sums. */
+    PGSGD_OPT_STRESS_ASYNC = 20,
+    /* Grid of the sampled-stress kernel: 0 = 8 blocks per SM (default);
+     * W in 1..8 = W whole waves of the blocks that fit on the GPU at once. */
+    PGSGD_OPT_STRESS_WAVES = 21
 } pgsgd_option;
 
 /* Device-resident graph: node records, packed step records, path table. */

@@ -19,7 +19,7 @@ PGSGD_OK, PGSGD_EINVAL, PGSGD_ERANGE, PGSGD_ENOMEM, PGSGD_ECUDA, PGSGD_ETIMEOUT,
 OPT = dict(coord_mode=1, updates_per_step=2, block=3, blocks_per_sm=4, updates_per_thread=5,
            atomic_updates=6, rebase=7, timing=8, max_concurrent=9,
            min_blocks=10, l2_fetch=11, store_mode=12, l2_hints=13, prefetch64=14, pipeline=15,
-           warp_merge=16, drf=17, srf=18)
+           warp_merge=16, drf=17, srf=18, async_depth=19, stress_async=20, stress_waves=21)
 
 
 BOPT = dict(mode=1, cuda_graph=2, block=3, updates_per_thread=4, chunk=5, max_concurrent=6,

@@ -429,6 +429,20 @@ int pgsgd_set_option(pgsgd_graph* g, int option, int64_t v) {
         case PGSGD_OPT_WARP_MERGE:
             g->warp_merge = v ? 1 : 0;
             return PGSGD_OK;
+        case PGSGD_OPT_ASYNC_DEPTH:
+            if (v != 0 && v != 2 && v != 3 && v != 4 && v != 6 && v != 8)
+                return fail(PGSGD_EINVAL, "async depth must be 0, 2, 3, 4, 6 or 8");
+            g->async_depth = (int)v;
+            return PGSGD_OK;
+        case PGSGD_OPT_STRESS_ASYNC:
+            if (v != 0 && v != 2 && v != 4 && v != 8)
+                return fail(PGSGD_EINVAL, "stress async depth must be 0, 2, 4 or 8");
+            g->stress_async = (int)v;
+            return PGSGD_OK;
+        case PGSGD_OPT_STRESS_WAVES:
+            if (v < 0 || v > 8) return fail(PGSGD_EINVAL, "stress waves must be in [0, 8]");
+            g->stress_waves = (int)v;
+            return PGSGD_OK;
         case PGSGD_OPT_DRF:
             if (v != 1 && v != 2 && v != 4 && v != 8) return fail(PGSGD_EINVAL, "data reuse factor must be 1, 2, 4 or 8");
             g->drf = (int)v;
@@ -466,6 +480,9 @@ int pgsgd_get_option(const pgsgd_graph* g, int option, int64_t* v) {
         case PGSGD_OPT_PREFETCH64: *v = g->pf64; return PGSGD_OK;
         case PGSGD_OPT_PIPELINE: *v = g->pipeline; return PGSGD_OK;
         case PGSGD_OPT_WARP_MERGE: *v = g->warp_merge; return PGSGD_OK;
+        case PGSGD_OPT_ASYNC_DEPTH: *v = g->async_depth; return PGSGD_OK;
+        case PGSGD_OPT_STRESS_ASYNC: *v = g->stress_async; return PGSGD_OK;
+        case PGSGD_OPT_STRESS_WAVES: *v = g->stress_waves; return PGSGD_OK;
         case PGSGD_OPT_DRF: *v = g->drf; return PGSGD_OK;
         case PGSGD_OPT_SRF: *v = g->srf; return PGSGD_OK;
         default: return fail(PGSGD_EINVAL, "unknown option %d", option);
@@ -560,6 +577,10 @@ int pgsgd_layout(pgsgd_graph* g, uint32_t iter_max, const double* eta, double et
     if (rc) return rc;
     if (g->pipeline && (g->warp_merge || g->drf > 1))
         return fail(PGSGD_EINVAL, "warp merging and data reuse run the plain update loop: set pipeline 0");
+    const bool async_loop = g->async_depth > 0 && !g->warp_merge && g->drf == 1;
+    if (async_loop && (g->pipeline || g->upt != 1))
+        return fail(PGSGD_EINVAL, "the asynchronous step-record loop runs one update per thread: set pipeline 0 "
+                                  "and updates_per_thread 1");
     // updates per iteration (Algorithm 1: 10 x steps) cut by the step reduction
     // factor; with data reuse the kernel counts selections of drf updates
     const uint64_t N_full = (uint64_t)g->updates_per_step * g->n_steps;
@@ -587,6 +608,7 @@ int pgsgd_layout(pgsgd_graph* g, uint32_t iter_max, const double* eta, double et
     // at 1 update per thread, 3 at 2 (no spills either way), else the
     // compiler's choice
     L.minb = g->min_blocks ? g->min_blocks : g->pipeline ? 1 : g->upt == 1 ? 4 : g->upt == 2 ? 3 : 1;
+    L.async_depth = async_loop ? g->async_depth : 0;
     L.store_mode = g->store_mode;
     L.l2_hints = g->l2_hints != 0;
     L.pf64 = g->pf64;
@@ -678,8 +700,18 @@ int pgsgd_stress(pgsgd_graph* g, uint32_t samples_per_step, uint64_t seed, pgsgd
     L.per_path = per_path ? g->d_per_path : nullptr;
     L.pf64 = (g->pf64 >> 2) & 3;
     L.block = 256;
+    L.async_depth = g->stress_async;
     const uint64_t want = (n_samples + 2 * 256 - 1) / (2 * 256);
     L.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)g->max_stress_blocks));
+    if (g->stress_waves > 0) {
+        // whole waves: every resident block slot busy until the end (a grid-stride loop spreads the samples evenly)
+        const int nb = stress_blocks_per_sm(L);
+        if (nb > 0) {
+            const int64_t wave = (int64_t)nb * g->sm_count;
+            const int64_t waves = std::max<int64_t>(1, std::min<int64_t>(g->stress_waves, g->max_stress_blocks / wave));
+            L.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)(waves * wave)));
+        }
+    }
     if (per_path) CK(cudaMemsetAsync(g->d_per_path, 0, (size_t)g->n_paths * 3 * 8, st), "per-path clear");
     CK(launch_stress(L, st), "stress kernel");
     double* tot = g->d_partials + 3 * (size_t)g->max_stress_blocks;

@@ -42,6 +42,7 @@ struct UpdateLaunch {
     bool pipeline;       // software-pipelined update loop
     bool wm;             // warp merging: one cooling coin per group of 32 updates
     int drf;             // data reuse factor (> 1: n_updates counts selections of drf updates)
+    int async_depth;     // > 0: step-record reads of the next async_depth updates in flight (cp.async)
 };
 
 struct StressLaunch {
@@ -56,6 +57,7 @@ struct StressLaunch {
     double* per_path;           // [P][3] or nullptr
     int block, grid;
     int pf64;                   // 64-byte L2 prefetch hint: bit 0 step loads, bit 1 node loads
+    int async_depth;            // > 0: step-record reads of the next async_depth samples in flight (cp.async)
 };
 
 // Shared memory of the staged path tables (offsets, Zipf thresholds, Zipf B, guide).
@@ -91,6 +93,7 @@ cudaError_t launch_debug_sample(const SamplerArgs& s, uint64_t u_begin, uint64_t
 cudaError_t launch_debug_sweep(const SamplerArgs& s, uint64_t u_begin, uint64_t count, const NodeRec* nodes,
                                float eta, float4* out, int sm_count, cudaStream_t st);
 cudaError_t launch_stress(const StressLaunch& L, cudaStream_t st);
+int stress_blocks_per_sm(const StressLaunch& L);
 cudaError_t launch_stress_finalize(const double* partials, int n, double* out3, cudaStream_t st);
 
 cudaError_t launch_dstress_forward(const SamplerArgs& s, const NodeRec* nodes, uint64_t n_pairs, double* partials,
@@ -157,6 +160,9 @@ struct pgsgd_graph {
     int pf64 = 7;
     int pipeline = 0;
     int warp_merge = 0;
+    int async_depth = 0;  // cp.async step-record ring depth of the update kernel (0 = off)
+    int stress_async = 0; // the same for the sampled-stress kernel
+    int stress_waves = 0; // stress grid: whole waves of resident blocks (0 = the former fixed grid)
     int drf = 1;          // data reuse factor
     int srf = 1;          // step reduction factor
 

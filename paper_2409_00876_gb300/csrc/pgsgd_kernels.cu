@@ -202,6 +202,80 @@ __global__ void __launch_bounds__(256, MINB) update_kernel(UpdateLaunch L) {
     }
 }
 
+// The update kernel with the step-record reads made asynchronous: every
+// thread keeps the step records of its next D updates in flight, copied
+// global -> shared memory by cp.async (16 bytes each, evict-first, 64-byte
+// prefetch hint) into slots of its own, so an outstanding read costs shared
+// memory instead of registers. A trip waits for its oldest group, reads the
+// two records from its slots, loads the two points and moves them as
+// finish_trip does, then draws the update D trips ahead and issues its reads
+// into the freed slots. Same updates per thread (u_begin + gtid + m * nthr),
+// same draws and moves as update_kernel<1, MINB, false>. Slots: after the
+// staged path tables, [D][2][blockDim] 16-byte records (16-byte aligned).
+__device__ __forceinline__ void cp_async_step(StepRec* dst, const StepRec* src, uint64_t pol) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint.L2::64B [%0], [%1], 16, %2;"
+                 :: "r"(d), "l"(src), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
+
+__host__ __device__ inline size_t async_slots_offset(uint32_t n_paths, uint32_t n_guide) {
+    return (update_smem_bytes(n_paths, n_guide) + 15) & ~(size_t)15;
+}
+
+template <int D, int MINB>
+__global__ void __launch_bounds__(256, MINB) update_kernel_async(UpdateLaunch L) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ ZipfConsts zc;
+    const PathTable pt = stage_paths(L.s, smem, zc);
+    SamplerArgs a = L.s;
+    a.zc = zc;
+    StepRec* slots = reinterpret_cast<StepRec*>(smem + async_slots_offset(L.s.n_paths, L.s.n_guide));
+    const uint32_t B = blockDim.x, tid = threadIdx.x;
+    const uint64_t pol_stream = L.l2_hints ? policy_evict_first() : 0;
+    const uint64_t pol_keep = L.l2_hints ? policy_evict_last() : 0;
+    const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t u_first = L.u_begin + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint64_t u_end = L.u_begin + L.n_updates;
+    const UpdateOpts o{L.eta, L.store_mode, L.pf64, L.atomic};
+    // per slot: the coin word of its update, or 0xffffffff when the slot holds no update
+    uint32_t w2s[D];
+    auto issue = [&](int k, uint64_t u) {
+        w2s[k] = 0xffffffffu;
+        if (u < u_end) {
+            const Pair pr = draw_pair(a, pt, u);
+            if (!pr.short_path) {
+                w2s[k] = pr.w2 & 0xfu;  // the coins are bits 0-3
+                cp_async_step(slots + (2 * k) * B + tid, a.steps + pr.base + pr.i, pol_stream);
+                cp_async_step(slots + (2 * k + 1) * B + tid, a.steps + pr.base + pr.j, pol_stream);
+            }
+        }
+        cp_async_commit();  // one group per slot, empty or not, so the group count stays exact
+    };
+#pragma unroll
+    for (int k = 0; k < D; ++k) issue(k, u_first + (uint64_t)k * nthr);
+    for (uint64_t base = u_first; base < u_end; base += (uint64_t)D * nthr) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            cp_async_wait<D - 1>();  // slot k's group (the oldest) has landed
+            if (w2s[k] != 0xffffffffu) {
+                TripDraws<1> d;
+                d.act[0] = true;
+                d.w2[0] = w2s[k];
+                d.gi[0] = d.gj[0] = 0;
+                StepRec si[1], sj[1];
+                si[0] = slots[(2 * k) * B + tid];
+                sj[0] = slots[(2 * k + 1) * B + tid];
+                finish_trip<1>(L.nodes, d, si, sj, o, pol_keep);
+            }
+            issue(k, base + (uint64_t)(k + D) * nthr);
+        }
+    }
+    cp_async_wait<0>();
+}
+
 // Warp merging (Section V-B3): the update kernel with one cooling coin per
 // group of 32 updates, shared by shuffle. The loop bound is the warp's first
 // update so all 32 lanes run every trip (u_begin is a multiple of 32).
@@ -339,6 +413,36 @@ __global__ void debug_sample_reuse_kernel(SamplerArgs a0, uint32_t R, uint64_t n
 
 // ---------------------------------------------------------------- sampled stress
 
+// Block reduction of (sum, squares, count) in a fixed order: warp shuffles,
+// then warp 0; the block's totals go to partials[3 * blockIdx.x ..].
+__device__ __forceinline__ void block_sums_to_partials(double sum, double sq, double cnt, double* partials) {
+    __shared__ double red[3][32];
+    for (int off = 16; off > 0; off >>= 1) {
+        sum += __shfl_down_sync(0xffffffffu, sum, off);
+        sq += __shfl_down_sync(0xffffffffu, sq, off);
+        cnt += __shfl_down_sync(0xffffffffu, cnt, off);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { red[0][warp] = sum; red[1][warp] = sq; red[2][warp] = cnt; }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        sum = lane < nw ? red[0][lane] : 0.0;
+        sq = lane < nw ? red[1][lane] : 0.0;
+        cnt = lane < nw ? red[2][lane] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) {
+            sum += __shfl_down_sync(0xffffffffu, sum, off);
+            sq += __shfl_down_sync(0xffffffffu, sq, off);
+            cnt += __shfl_down_sync(0xffffffffu, cnt, off);
+        }
+        if (lane == 0) {
+            partials[3 * (uint64_t)blockIdx.x] = sum;
+            partials[3 * (uint64_t)blockIdx.x + 1] = sq;
+            partials[3 * (uint64_t)blockIdx.x + 2] = cnt;
+        }
+    }
+}
+
 template <int SPT>
 __global__ void stress_kernel(StressLaunch L) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -423,32 +527,100 @@ __global__ void stress_kernel(StressLaunch L) {
         atomicAdd(L.per_path + 3 * (uint64_t)cur_p + 1, pq);
         atomicAdd(L.per_path + 3 * (uint64_t)cur_p + 2, pc);
     }
-    // block reduction in a fixed order: warp shuffles, then warp 0
-    __shared__ double red[3][32];
-    for (int off = 16; off > 0; off >>= 1) {
-        sum += __shfl_down_sync(0xffffffffu, sum, off);
-        sq += __shfl_down_sync(0xffffffffu, sq, off);
-        cnt += __shfl_down_sync(0xffffffffu, cnt, off);
+    block_sums_to_partials(sum, sq, cnt, L.partials);
+}
+
+// The sampled-stress kernel with the step-record reads made asynchronous, as
+// in update_kernel_async: every thread keeps the step records of its next D
+// samples in flight (cp.async into slots of its own in shared memory), then
+// reads the two node records (read-only here) and adds the term. Same
+// samples in the same per-thread order as stress_kernel, so the same sums.
+// Slots: after the two staged offset tables, [D][2][blockDim] records.
+template <int D>
+__global__ void __launch_bounds__(256) stress_kernel_async(StressLaunch L) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t* s_soff = reinterpret_cast<uint64_t*>(smem);   // [P + 1] sample offsets
+    uint64_t* s_poff = s_soff + L.n_paths + 1;              // [P + 1] step offsets
+    StepRec* slots = reinterpret_cast<StepRec*>(s_poff + L.n_paths + 1);  // 2 (P + 1) x 8 bytes: 16-byte aligned
+    for (uint32_t k = threadIdx.x; k <= L.n_paths; k += blockDim.x) {
+        s_soff[k] = L.sample_off[k];
+        s_poff[k] = L.path_off[k];
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) { red[0][warp] = sum; red[1][warp] = sq; red[2][warp] = cnt; }
     __syncthreads();
-    if (warp == 0) {
-        const int nw = blockDim.x >> 5;
-        sum = lane < nw ? red[0][lane] : 0.0;
-        sq = lane < nw ? red[1][lane] : 0.0;
-        cnt = lane < nw ? red[2][lane] : 0.0;
-        for (int off = 16; off > 0; off >>= 1) {
-            sum += __shfl_down_sync(0xffffffffu, sum, off);
-            sq += __shfl_down_sync(0xffffffffu, sq, off);
-            cnt += __shfl_down_sync(0xffffffffu, cnt, off);
+    const uint32_t B = blockDim.x, tid = threadIdx.x;
+    const uint64_t pol_stream = policy_evict_first();
+    const uint64_t pol_keep = policy_evict_last();
+    const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t first = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    double sum = 0.0, sq = 0.0, cnt = 0.0;
+    uint32_t cur_p = 0xffffffffu;
+    double ps = 0.0, pq = 0.0, pc = 0.0;
+    // per slot: path | endpoint coins << 30 of its sample, or 0xffffffff when empty
+    uint32_t tag[D];
+    auto issue = [&](int k, uint64_t Q) {
+        tag[k] = 0xffffffffu;
+        if (Q < L.n_samples) {
+            const uint32_t p = find_path(s_soff, L.n_paths, Q);
+            const uint64_t q = Q - s_soff[p];
+            const uint64_t off = s_poff[p];
+            const uint64_t n = s_poff[p + 1] - off;
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), 0x80000000u | p, 0u),
+                                          L.key0, L.key1);
+            const uint64_t i = mulhi64((uint64_t)w.x | ((uint64_t)w.y << 32), n);
+            const uint64_t x = mulhi64(((uint64_t)w.w << 32) | (w.z & ~15u), n - 1);
+            const uint64_t j = x + (x >= i);
+            tag[k] = p | ((w.z & 3u) << 30);  // p < 2^14 (the path table lives in shared memory)
+            cp_async_step(slots + (2 * k) * B + tid, L.steps + off + i, pol_stream);
+            cp_async_step(slots + (2 * k + 1) * B + tid, L.steps + off + j, pol_stream);
         }
-        if (lane == 0) {
-            L.partials[3 * (uint64_t)blockIdx.x] = sum;
-            L.partials[3 * (uint64_t)blockIdx.x + 1] = sq;
-            L.partials[3 * (uint64_t)blockIdx.x + 2] = cnt;
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int k = 0; k < D; ++k) issue(k, first + (uint64_t)k * nthr);
+    for (uint64_t base = first; base < L.n_samples; base += (uint64_t)D * nthr) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            cp_async_wait<D - 1>();
+            const uint32_t tg = tag[k];
+            if (tg != 0xffffffffu) {
+                const StepRec si = slots[(2 * k) * B + tid], sj = slots[(2 * k + 1) * B + tid];
+                const uint32_t p = tg & 0x3fffffffu, ei = (tg >> 30) & 1u, ej = tg >> 31;
+                const int64_t pa = endpoint_pos(si, ei), pb = endpoint_pos(sj, ej);
+                const int64_t d = pa > pb ? pa - pb : pb - pa;
+                if (d != 0) {
+                    const float2 va = load_point(L.nodes + step_node(si), ei, pol_keep, L.pf64 & 2);
+                    const float2 vb = load_point(L.nodes + step_node(sj), ej, pol_keep, L.pf64 & 2);
+                    const float dx = __ll2float_rn((int64_t)si.ax - (int64_t)sj.ax) + (va.x - vb.x);
+                    const float dy = va.y - vb.y;
+                    const float df = __ll2float_rn(d);
+                    const float t = (sqrtf(dx * dx + dy * dy) - df) / df;
+                    const float term = t * t;
+                    sum += (double)term;
+                    sq += (double)term * (double)term;
+                    cnt += 1.0;
+                    if (L.per_path) {
+                        if (p != cur_p) {
+                            if (cur_p != 0xffffffffu) {
+                                atomicAdd(L.per_path + 3 * (uint64_t)cur_p, ps);
+                                atomicAdd(L.per_path + 3 * (uint64_t)cur_p + 1, pq);
+                                atomicAdd(L.per_path + 3 * (uint64_t)cur_p + 2, pc);
+                            }
+                            cur_p = p; ps = pq = pc = 0.0;
+                        }
+                        ps += (double)term; pq += (double)term * (double)term; pc += 1.0;
+                    }
+                }
+            }
+            issue(k, base + (uint64_t)(k + D) * nthr);
         }
     }
+    cp_async_wait<0>();
+    if (L.per_path && cur_p != 0xffffffffu) {
+        atomicAdd(L.per_path + 3 * (uint64_t)cur_p, ps);
+        atomicAdd(L.per_path + 3 * (uint64_t)cur_p + 1, pq);
+        atomicAdd(L.per_path + 3 * (uint64_t)cur_p + 2, pc);
+    }
+    block_sums_to_partials(sum, sq, cnt, L.partials);
 }
 
 // Sum the per-block partials in a fixed order (one block of 256 threads).
@@ -569,8 +741,30 @@ static cudaError_t launch_with_smem(K kernel, const UpdateLaunch& L, cudaStream_
     return cudaGetLastError();
 }
 
+template <int D, int MINB>
+static cudaError_t launch_update_async_t(const UpdateLaunch& L, cudaStream_t st) {
+    const size_t smem = async_slots_offset(L.s.n_paths, L.s.n_guide) + (size_t)D * 2 * L.block * sizeof(StepRec);
+    cudaError_t e = cudaFuncSetAttribute(update_kernel_async<D, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    update_kernel_async<D, MINB><<<L.grid, L.block, smem, st>>>(L);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_update(const UpdateLaunch& L, cudaStream_t st) {
     if (L.n_updates == 0) return cudaSuccess;
+    if (L.async_depth > 0) {
+        switch (L.async_depth * 10 + L.minb) {
+            case 24: return launch_update_async_t<2, 4>(L, st);
+            case 34: return launch_update_async_t<3, 4>(L, st);
+            case 44: return launch_update_async_t<4, 4>(L, st);
+            case 45: return launch_update_async_t<4, 5>(L, st);
+            case 64: return launch_update_async_t<6, 4>(L, st);
+            case 84: return launch_update_async_t<8, 4>(L, st);
+            case 43: return launch_update_async_t<4, 3>(L, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     if (L.drf > 1) {
         switch (L.drf) {
             case 2: return launch_with_smem(update_reuse_kernel<2>, L, st);
@@ -647,7 +841,45 @@ cudaError_t launch_debug_sweep(const SamplerArgs& s, uint64_t u_begin, uint64_t 
     return cudaGetLastError();
 }
 
+template <int D>
+static cudaError_t launch_stress_async_t(const StressLaunch& L, cudaStream_t st) {
+    const size_t smem = stress_smem_bytes(L.n_paths) + (size_t)D * 2 * L.block * sizeof(StepRec);
+    cudaError_t e = cudaFuncSetAttribute(stress_kernel_async<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    stress_kernel_async<D><<<L.grid, L.block, smem, st>>>(L);
+    return cudaGetLastError();
+}
+
+// Resident 256-thread blocks per SM of the stress kernel that L.async_depth selects.
+int stress_blocks_per_sm(const StressLaunch& L) {
+    int nb = 0;
+    const size_t base = stress_smem_bytes(L.n_paths);
+    cudaError_t e = cudaSuccess;
+    switch (L.async_depth) {
+        case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stress_kernel<2>, L.block, base); break;
+        case 2: e = cudaFuncSetAttribute(stress_kernel_async<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000);
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stress_kernel_async<2>, L.block, base + 2 * 2 * L.block * 16);
+            break;
+        case 4: e = cudaFuncSetAttribute(stress_kernel_async<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000);
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stress_kernel_async<4>, L.block, base + 4 * 2 * L.block * 16);
+            break;
+        case 8: e = cudaFuncSetAttribute(stress_kernel_async<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000);
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stress_kernel_async<8>, L.block, base + 8 * 2 * L.block * 16);
+            break;
+        default: return 0;
+    }
+    return e == cudaSuccess ? nb : 0;
+}
+
 cudaError_t launch_stress(const StressLaunch& L, cudaStream_t st) {
+    switch (L.async_depth) {
+        case 2: return launch_stress_async_t<2>(L, st);
+        case 4: return launch_stress_async_t<4>(L, st);
+        case 8: return launch_stress_async_t<8>(L, st);
+        case 0: break;
+        default: return cudaErrorInvalidValue;
+    }
     const size_t smem = stress_smem_bytes(L.n_paths);
     cudaError_t e = cudaFuncSetAttribute(stress_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);

@@ -52,18 +52,24 @@ def test_linear_path_converges_on_gpu(pg):
     assert st["mean"] < 1e-3
 
 
-def test_tiny_layout_quality_matches_oracle(pg):
+def test_tiny_layout_quality_matches_oracle_within_1_percent(pg):
+    """The 1 % target resolved: 40 layout seeds on each side (the oracle
+    sequential, the GPU lock-free, each seed's draws the same on both), so
+    that two standard errors of the difference of the means, from the
+    measured seed-to-seed spreads, come below 1 % of the oracle's mean; the
+    bar is then 1 %."""
     g = make_graph("tiny")
     ref = []
     got = []
-    for seed in range(1, 6):
+    for seed in range(1, 41):
         xy, _ = O.layout(g, g.init_xy, T=T, theta=0.99, seed=seed)
         ref.append(O.sampled_stress(g, xy, seed=7)["mean"])
         got.append(_layout_stress(pg, g, seed, 100, 7)[0]["mean"])
     ref, got = np.array(ref), np.array(got)
-    # the seed-to-seed spread of the oracle itself sets how close means can be
-    se = np.hypot(ref.std(ddof=1), got.std(ddof=1)) / np.sqrt(len(ref))
-    assert abs(got.mean() - ref.mean()) <= max(0.01 * ref.mean(), 3 * se), (got, ref)
+    se = np.sqrt(ref.var(ddof=1) / len(ref) + got.var(ddof=1) / len(got))
+    print("tiny", got.mean(), ref.mean(), (got.mean() - ref.mean()) / ref.mean(), 2 * se / ref.mean())
+    assert 2 * se <= 0.01 * ref.mean(), (se, ref.mean())  # the comparison resolves 1 %
+    assert abs(got.mean() - ref.mean()) <= 0.01 * ref.mean(), (got.mean(), ref.mean())
 
 
 @pytest.mark.parametrize("name", ["mid", "chrom"])

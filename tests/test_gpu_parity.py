@@ -159,6 +159,39 @@ def test_stress_kernel_matches_oracle_on_same_layout(pg, name):
     np.testing.assert_allclose(got["per_path"][:, 0], want["per_path"][:, 0], rtol=1e-4, atol=1e-12)
 
 
+@pytest.mark.parametrize("opts", [dict(stress_async=2), dict(stress_async=4), dict(stress_async=8),
+                                  dict(stress_waves=2), dict(stress_async=4, stress_waves=1),
+                                  dict(stress_async=8, stress_waves=3)])
+def test_stress_kernel_shapes_match_the_oracle(pg, opts):
+    """Every compiled shape of the sampled-stress kernel (asynchronous
+    step-record reads, whole-wave grids) on the same layout and samples as
+    the oracle's Eq. 2, with its per-path sums."""
+    g = _graph("mid")
+    G = _gpu_graph(pg, g)
+    G.layout(T, theta=THETA, seed=2, iter_end=3)
+    xy = G.get_coords()
+    want = O.sampled_stress(g, xy, per_step=10, seed=13, per_path=True)
+    base = G.stress(10, seed=13)
+    for k, v in opts.items():
+        G.set_option(k, v)
+    got = G.stress(10, seed=13, per_path=True)
+    assert got["n_valid"] == want["n_valid"] == base["n_valid"]
+    assert got["n_skipped"] == want["n_skipped"]
+    assert abs(got["mean"] - want["mean"]) <= 1e-4 * want["mean"]
+    assert abs(got["mean"] - base["mean"]) <= 1e-9 * base["mean"]  # the same terms, summed in another order
+    assert abs(got["std"] - want["std"]) <= 1e-3 * want["std"]
+    np.testing.assert_array_equal(got["per_path"][:, 2], want["per_path"][:, 2])
+    np.testing.assert_allclose(got["per_path"][:, 0], want["per_path"][:, 0], rtol=1e-4, atol=1e-12)
+
+
+def test_stress_shape_options_are_checked(pg):
+    from paper_2409_00876_gb300 import PgsgdError
+    G = _gpu_graph(pg, _graph("tiny"))
+    for name, bad in [("stress_async", 3), ("stress_async", 16), ("stress_waves", 9), ("stress_waves", -1)]:
+        with pytest.raises(PgsgdError):
+            G.set_option(name, bad)
+
+
 def test_coords_round_trip_exact(pg):
     g = _graph("tiny")
     for mode in (0, 1):

@@ -77,6 +77,12 @@ def _sparse_iteration(pg, g, drf, wm, srf, t=10, seed=3, **opts):
     (1, 0, dict(pipeline=1)), (1, 0, dict(pipeline=1, updates_per_thread=2)),
     (1, 0, dict(updates_per_thread=2)), (1, 0, dict(updates_per_thread=4)), (1, 0, dict(min_blocks=1)),
     (1, 0, dict(min_blocks=6)), (1, 0, dict(updates_per_thread=2, min_blocks=1)), (1, 1, dict(updates_per_thread=4)),
+    # the asynchronous step-record loop: one block of 256 threads, so every thread
+    # runs 4 updates and cycles through its slots
+    (1, 0, dict(async_depth=2, max_concurrent=256)), (1, 0, dict(async_depth=3, max_concurrent=256)),
+    (1, 0, dict(async_depth=4, max_concurrent=256)), (1, 0, dict(async_depth=6, max_concurrent=256)),
+    (1, 0, dict(async_depth=8, max_concurrent=256)), (1, 0, dict(async_depth=4, min_blocks=3)),
+    (1, 0, dict(async_depth=4, min_blocks=5)),
 ])
 def test_kernel_updates_match_the_oracle_on_a_sparse_iteration(pg, mid, drf, wm, opts):
     srf = -(-10 * mid.n_steps // 1024)  # about 1024 selections on 220 k nodes
@@ -129,3 +135,9 @@ def test_variant_options_are_checked(pg):
     G.set_option("drf", 1)
     with pytest.raises(PgsgdError, match="reuse is off"):
         G.debug_sample_reuse(0, T, 0.99, 1, 0, 10)
+    with pytest.raises(PgsgdError, match="async depth"):
+        G.set_option("async_depth", 5)
+    G.set_option("async_depth", 4)
+    G.set_option("updates_per_thread", 2)
+    with pytest.raises(PgsgdError, match="one update per thread"):
+        G.layout(T)
