@@ -424,6 +424,11 @@ def run_gpu(args):
         # time x clock: equal across GPUs when a difference in time is a difference in clock
         ph["ms_x_ghz"] = ph["ms_per_step"] * ph["sm_mhz_median"] / 1e3
     vs_oracle = stress_vs_oracle(G, args.config) if rank == 0 else None
+    # the stress kernel makes the same random reads as an update (two step
+    # records, two node points) with no arithmetic of note and no writes: its
+    # rate on this GPU is the measured gather rate the update kernel is held to
+    gather_ref = {"kernel": "stress_kernel (Eq. 2): the same two random step-record reads and two node reads "
+                            "per unit, no moves, no writes", "units_per_s": phases["stress"]["samples_per_s"]}
     ms_max = max_over_ranks(ms, dev)
     value = aggregate_rate(updates_per_step * args.steps, ms, dev)
 
@@ -435,9 +440,11 @@ def run_gpu(args):
     updates_per_launch = upd / max(launches, 1)
     achieved = BYTES_PER_UPDATE * updates_per_launch / (per_launch_ms / 1e3) / 1e9
     gather = hbm_gather(pg) if args.config in ("chrom", "prof") else None
+    # ncu DRAM bytes per update, captured on the 2 M-node profiling graph (the same
+    # record sizes and access pattern, 1 GB resident) and scaled to this launch's updates
     traffic = None
-    tpath = os.path.join(ROOT, "profiles", f"update_kernel_traffic_{args.config}.json")
-    if os.path.exists(tpath):
+    tpath = os.path.join(ROOT, "profiles", "update_kernel_traffic_prof.json")
+    if os.path.exists(tpath) and args.config in ("chrom", "prof"):
         tr = json.load(open(tpath))
         if tr.get("kernel_rev") == kernel_revision():
             traffic = tr["dram_bytes_per_update"] * updates_per_launch
@@ -473,7 +480,8 @@ def run_gpu(args):
             "layout_only_updates_per_s": upd / (upd_ms / 1e3) if upd_ms > 0 else None,
             "stress_vs_oracle": vs_oracle,
             "roofline": roofline_for(args.config, achieved, peak, peak_kind, traffic, per_launch_ms, gather,
-                                     2 * updates_per_launch / (per_launch_ms / 1e3)),
+                                     2 * updates_per_launch / (per_launch_ms / 1e3), gather_ref,
+                                     updates_per_launch / (per_launch_ms / 1e3)),
             "clocks": clk,
             "phases": phases,
             "gpu_launches": gpu_launches,
@@ -751,18 +759,19 @@ def run_batch(args):
 
 
 def hbm_gather(pg):
-    """Random-read ceilings of HBM measured in-repo (pgsgd_hbm_gather_bandwidth,
-    4 GiB buffer): reads/s of the update kernel's step-record form (16 bytes,
-    64-byte prefetch hint), of the same read without the hint and of whole
-    random 64-byte blocks; best of 4 and 8 resident blocks per SM."""
-    best = {m: max(pg.hbm_gather_rate(4 << 30, 4, m, b) for b in (4, 8)) for m in (0, 1, 2)}
-    return {"reads_per_s_16B_hint64": best[0], "reads_per_s_16B_nohint": best[1],
-            "reads_per_s_64B_block": best[2],
-            "gbs_16B_hint64_as_32B_sectors": best[0] * 32 / 1e9, "gbs_16B_hint64_as_64B_accesses": best[0] * 64 / 1e9,
-            "gbs_64B_block": best[2] * 64 / 1e9}
+    """Random-read ceiling of HBM measured in-repo (pgsgd_hbm_gather_bandwidth,
+    4 GiB buffer): reads/s of 16-byte step-record-like reads, two per unit on
+    one of 90 "paths" (mode 0), and with two L2-resident 8-byte node-like reads
+    per unit besides (mode 1); best of 8, 16 and 32 blocks per SM."""
+    best = {m: max(pg.hbm_gather_rate(4 << 30, 4, m, b) for b in (8, 16, 32)) for m in (0, 1)}
+    return {"reads_per_s": best[0], "reads_per_s_with_node_reads": best[1],
+            "gbs_as_32B_sectors": best[0] * 32 / 1e9, "gbs_as_64B_accesses": best[0] * 64 / 1e9,
+            "pattern": "16-byte reads, evict-first, 64-byte prefetch hint; two per unit, uniform on one of 90 "
+                       "equal paths of a 4 GiB buffer (Philox4x32-10 indices)"}
 
 
-def roofline_for(config, achieved, peak, peak_kind, traffic, launch_ms, gather=None, step_reads_per_s=None):
+def roofline_for(config, achieved, peak, peak_kind, traffic, launch_ms, gather=None, step_reads_per_s=None,
+                 gather_ref=None, updates_per_s=None):
     """HBM roofline; for graphs whose records fit in L2 (mid, tiny) the bound is
     L2, against the L2 read bandwidth measured in-repo (pgsgd_l2_bandwidth).
     With `gather` (hbm_gather) the update kernel's random step-record reads
@@ -773,12 +782,16 @@ def roofline_for(config, achieved, peak, peak_kind, traffic, launch_ms, gather=N
          "traffic": traffic, "kernel": "update_kernel", "bytes_per_update_model": BYTES_PER_UPDATE,
          "peak_kind": peak_kind, "launch_ms": launch_ms}
     if gather:
-        r["random_gather_gbs"] = gather["gbs_16B_hint64_as_32B_sectors"]
-        r["frac_of_random_gather"] = achieved / r["random_gather_gbs"]
+        r["random_gather_gbs"] = gather["gbs_as_32B_sectors"]
         r["random_gather"] = gather
         if step_reads_per_s:
+            # the update kernel's step-record reads against the probe's rate of the same reads; as GB/s at
+            # 32 B per read (the unit of random_gather_gbs) this is frac_of_random_gather
             r["step_reads_per_s"] = step_reads_per_s
-            r["step_read_frac_of_random_read_rate"] = step_reads_per_s / gather["reads_per_s_16B_hint64"]
+            r["frac_of_random_gather"] = step_reads_per_s / gather["reads_per_s"]
+            r["frac_of_random_gather_with_node_reads"] = step_reads_per_s / gather["reads_per_s_with_node_reads"]
+    if gather_ref and updates_per_s:
+        r["gather_reference"] = dict(gather_ref, update_frac=updates_per_s / gather_ref["units_per_s"])
     if config in ("mid", "tiny"):
         import paper_2409_00876_gb300 as pg
         stream = max(pg.l2_bandwidth(mib << 20, 20, 0) for mib in (16, 32, 64))

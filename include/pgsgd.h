@@ -55,9 +55,12 @@ typedef enum pgsgd_option {
     /* Update-kernel launch shape: threads per block (64..256, multiple of
      * 32; default 256), blocks per SM in the grid (default 32: many short
      * blocks let the block scheduler balance the two dies), and
-     * updates each thread keeps in flight per loop trip (1, 2 or 4; default 1,
-     * which with 4 resident blocks per SM ran the chromosome layout 2.7 %
-     * faster than 2 with 3). */
+     * updates each thread keeps in flight per loop trip (1, 2 or 4; default 0
+     * = automatic: 2 with the pipelined loop, PGSGD_OPT_PIPELINE, else 1; the
+     * pipelined loop at 2 ran the full chromosome layout
+     * in 6.58 s against 6.74 s for 1 update per thread unpipelined with 4
+     * resident blocks per SM, the next best shape of a sweep over updates per
+     * thread, register budgets, grid sizes and asynchronous step reads). */
     PGSGD_OPT_BLOCK = 3,
     PGSGD_OPT_BLOCKS_PER_SM = 4,
     PGSGD_OPT_UPDATES_PER_THREAD = 5,
@@ -86,7 +89,8 @@ typedef enum pgsgd_option {
      * compiled variants are 1, 4, 6 for 1 update per thread, 1, 3, 4 for 2
      * and 1, 2, 3 for 4; the pipelined loop: 1, 3 for 1 and 1, 2 for 2).
      * Default 0 = automatic: for the plain loop 4 at 1 update per thread and
-     * 3 at 2 (no spills), else 1. */
+     * 3 at 2 (no spills); for the pipelined loop 2 at 2 updates per thread
+     * (98 registers, no spills); else 1. */
     PGSGD_OPT_MIN_BLOCKS = 10,
     /* L2 fetch granularity in bytes set on the current context before each
      * layout (cudaLimitMaxL2FetchGranularity; 0 = leave it unchanged, the
@@ -114,7 +118,10 @@ typedef enum pgsgd_option {
     /* 1 = software-pipelined update loop: each thread issues a trip's
      * step-record loads, then draws the next trip's pairs while they are in
      * flight (same draws and moves; compiled for updates per thread / min
-     * blocks 1/1, 1/3, 2/1, 2/2 and 4/1). Default 0. */
+     * blocks 1/1, 1/3, 2/1, 2/2 and 4/1). Default -1 = automatic: the
+     * pipelined loop for the plain method, the plain loop under warp
+     * merging, data reuse or PGSGD_OPT_ASYNC_DEPTH, which need it (setting 1
+     * with them is an error). */
     PGSGD_OPT_PIPELINE = 15,
     /* Warp merging (Section V-B3): 1 = the cooling coin of update u is bit 0
      * of w2 of update 32 floor(u / 32), so a warp's 32 consecutive updates
@@ -401,20 +408,21 @@ int pgsgd_l2_bandwidth(uint64_t bytes, uint32_t reps, int mode, double *gbs, voi
 
 /*
  * Measurement helper, no counterpart in the paper: the rate of random reads
- * from HBM (*loads_per_s, host: reads completed per second), the ceiling of a
- * kernel bound by random record reads, as the update kernel is on graphs
- * whose 16-byte step records are far larger than L2 (the memory-bound
- * random access of Section III-B). Allocates a `bytes` buffer (1..64 GiB,
- * keep it several times the L2 size), then times `reps` (1..100) launches of
- * blocks_per_sm (1..8) 256-thread blocks per SM, 512 random reads per thread,
- * four in flight. mode 0 = a 16-byte load with the evict-first policy and the
- * 64-byte L2 prefetch-size hint (the form of the update kernel's step-record
- * read); 1 = the same load without the hint; 2 = a random 64-byte block read
- * as four coalesced 16-byte pieces by four lanes (one read = one block).
- * Multiply by 32 (the sector a 16-byte read touches) or 64 (the DRAM access
- * it costs with the hint) for GB/s. Synchronous; frees everything it
- * allocated. PGSGD_EINVAL for arguments out of range, PGSGD_ENOMEM when the
- * buffer cannot be allocated.
+ * from HBM (*loads_per_s, host: reads of the large buffer completed per
+ * second), the ceiling of a kernel bound by random record reads, as the
+ * update and stress kernels are on graphs whose 16-byte step records are far
+ * larger than L2 (the memory-bound random access of Section III-B).
+ * Allocates a `bytes` buffer (1..64 GiB, keep it several times the L2 size)
+ * of 16-byte records cut into 90 equal "paths", and times `reps` (1..100)
+ * launches of blocks_per_sm (1..64) 256-thread blocks per SM over
+ * 4 x records units: unit Q takes path Q mod 90 and two records uniform on it
+ * from one Philox4x32-10 block, read as the step records are (16-byte load,
+ * evict-first, 64-byte L2 prefetch hint). mode 0 = those two reads; mode 1 =
+ * plus two random 8-byte reads from an 88 MB array kept in L2 (an update's
+ * two point reads). Multiply by 32 (the sector a read touches) or 64 (the
+ * DRAM access it costs with the hint) for GB/s. Synchronous; frees
+ * everything it allocated. PGSGD_EINVAL for arguments out of range,
+ * PGSGD_ENOMEM when the buffers cannot be allocated.
  */
 int pgsgd_hbm_gather_bandwidth(uint64_t bytes, uint32_t reps, int mode, int blocks_per_sm,
                                double *loads_per_s, void *cuda_stream);

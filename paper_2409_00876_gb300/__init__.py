@@ -35,9 +35,10 @@ def l2_bandwidth(bytes_=64 << 20, reps=20, mode=0, stream=None):
     return out.value
 
 
-def hbm_gather_rate(bytes_=4 << 30, reps=4, mode=0, blocks_per_sm=8, stream=None):
-    """Random reads per second from an HBM buffer of bytes_ (mode 0: 16-byte
-    loads with the 64-byte prefetch hint, 1: without it, 2: 64-byte blocks)."""
+def hbm_gather_rate(bytes_=4 << 30, reps=4, mode=0, blocks_per_sm=32, stream=None):
+    """Random step-record-like reads per second from an HBM buffer of bytes_
+    (two random 16-byte reads per unit within one of 90 "paths"; mode 1 adds
+    two L2-resident 8-byte reads per unit)."""
     lib = N.load()
     out = C.c_double()
     N.check(lib.pgsgd_hbm_gather_bandwidth(int(bytes_), int(reps), int(mode), int(blocks_per_sm), C.byref(out),

@@ -392,7 +392,8 @@ int pgsgd_set_option(pgsgd_graph* g, int option, int64_t v) {
             g->blocks_per_sm = (int)v;
             return PGSGD_OK;
         case PGSGD_OPT_UPDATES_PER_THREAD:
-            if (v != 1 && v != 2 && v != 4) return fail(PGSGD_EINVAL, "updates per thread must be 1, 2 or 4");
+            if (v != 0 && v != 1 && v != 2 && v != 4)
+                return fail(PGSGD_EINVAL, "updates per thread must be 0 (automatic), 1, 2 or 4");
             g->upt = (int)v;
             return PGSGD_OK;
         case PGSGD_OPT_ATOMIC_UPDATES:
@@ -424,7 +425,8 @@ int pgsgd_set_option(pgsgd_graph* g, int option, int64_t v) {
             g->pf64 = (int)v;
             return PGSGD_OK;
         case PGSGD_OPT_PIPELINE:
-            g->pipeline = v ? 1 : 0;
+            if (v < -1 || v > 1) return fail(PGSGD_EINVAL, "pipeline must be -1 (automatic), 0 or 1");
+            g->pipeline = (int)v;
             return PGSGD_OK;
         case PGSGD_OPT_WARP_MERGE:
             g->warp_merge = v ? 1 : 0;
@@ -575,10 +577,16 @@ int pgsgd_layout(pgsgd_graph* g, uint32_t iter_max, const double* eta, double et
     const float th = (float)theta;
     rc = ensure_zipf(g, th, st);
     if (rc) return rc;
-    if (g->pipeline && (g->warp_merge || g->drf > 1))
+    // launch shape: the automatic choice (pipeline -1, updates per thread 0) is
+    // the pipelined loop at 2 updates per thread for the plain method, one
+    // update per thread otherwise
+    const bool plain = !g->warp_merge && g->drf == 1;
+    if (g->pipeline == 1 && !plain)
         return fail(PGSGD_EINVAL, "warp merging and data reuse run the plain update loop: set pipeline 0");
-    const bool async_loop = g->async_depth > 0 && !g->warp_merge && g->drf == 1;
-    if (async_loop && (g->pipeline || g->upt != 1))
+    const bool async_loop = g->async_depth > 0 && plain;
+    const int pipe = g->pipeline >= 0 ? g->pipeline : (plain && !async_loop ? 1 : 0);
+    const int upt = g->upt > 0 ? g->upt : (pipe ? 2 : 1);
+    if (async_loop && (pipe || upt != 1))
         return fail(PGSGD_EINVAL, "the asynchronous step-record loop runs one update per thread: set pipeline 0 "
                                   "and updates_per_thread 1");
     // updates per iteration (Algorithm 1: 10 x steps) cut by the step reduction
@@ -593,7 +601,7 @@ int pgsgd_layout(pgsgd_graph* g, uint32_t iter_max, const double* eta, double et
     if (cap == -1) cap = std::max<int64_t>(2048, (int64_t)g->n_nodes / 2);
     if (cap > 0) {
         // the cap counts updates: a thread keeps upt updates, or one selection of drf updates, in flight
-        const int64_t per_block = (int64_t)g->block * (g->drf > 1 ? g->drf : g->upt);
+        const int64_t per_block = (int64_t)g->block * (g->drf > 1 ? g->drf : upt);
         const int64_t gmax = std::max<int64_t>(1, cap / per_block);
         if (gmax < grid) grid = (int)gmax;
     }
@@ -603,16 +611,16 @@ int pgsgd_layout(pgsgd_graph* g, uint32_t iter_max, const double* eta, double et
     L.n_updates = N;
     L.block = g->block;
     L.grid = grid;
-    L.upt = g->upt;
+    L.upt = upt;
     // automatic register budget for the plain loop: 4 resident blocks per SM
     // at 1 update per thread, 3 at 2 (no spills either way), else the
     // compiler's choice
-    L.minb = g->min_blocks ? g->min_blocks : g->pipeline ? 1 : g->upt == 1 ? 4 : g->upt == 2 ? 3 : 1;
+    L.minb = g->min_blocks ? g->min_blocks : pipe ? (upt == 2 ? 2 : 1) : upt == 1 ? 4 : upt == 2 ? 3 : 1;
     L.async_depth = async_loop ? g->async_depth : 0;
     L.store_mode = g->store_mode;
     L.l2_hints = g->l2_hints != 0;
     L.pf64 = g->pf64;
-    L.pipeline = g->pipeline != 0;
+    L.pipeline = pipe != 0;
     L.wm = g->warp_merge != 0;
     L.drf = g->drf;
     L.atomic = g->atomic != 0;

@@ -148,7 +148,7 @@ struct pgsgd_graph {
     int updates_per_step = 10;
     int block = 256;
     int blocks_per_sm = 32;
-    int upt = 1;
+    int upt = 0;          // 0 = automatic (2 with the pipelined loop, else 1)
     int atomic = 0;
     int rebase = 1;
     int timing = 0;
@@ -158,7 +158,7 @@ struct pgsgd_graph {
     int store_mode = 1;  // 64-bit atomic exchange: measured fastest replace-store
     int l2_hints = 1;
     int pf64 = 7;
-    int pipeline = 0;
+    int pipeline = -1;    // -1 = automatic (the pipelined loop for the plain method)
     int warp_merge = 0;
     int async_depth = 0;  // cp.async step-record ring depth of the update kernel (0 = off)
     int stress_async = 0; // the same for the sampled-stress kernel

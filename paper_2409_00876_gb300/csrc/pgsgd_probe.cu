@@ -4,9 +4,9 @@
 // records). Two patterns over one L2-resident buffer: streaming 16-byte
 // vector loads (each warp reads 512 contiguous bytes) and random 16-byte loads
 // (one 32-byte sector each, as the update kernel's record reads).
-// HBM random-read rate: random 16-byte loads from a multi-GB buffer (the
-// step-record reads of the chromosome graph, whose 7.5 GB of step records
-// are far beyond L2), the ceiling for a kernel bound by random sectors.
+// HBM random-read rate: random 16-byte loads from a multi-GB buffer in the
+// pattern of the step-record reads of a chromosome-scale graph (7.5 GB of
+// step records, far beyond L2), the ceiling for a kernel bound by them.
 #include <algorithm>
 #include <cstdint>
 
@@ -15,6 +15,9 @@
 
 namespace pgsgd {
 namespace {
+
+constexpr uint32_t kGatherPaths = 90;          // "paths" of the gather probe's buffer
+constexpr uint32_t kGatherSmall = 5500000;     // node-sized array: 88 MB of 16-byte records
 
 // Four independent 16-byte loads in flight per thread; a warp reads 512
 // contiguous bytes per load instruction.
@@ -65,38 +68,37 @@ __global__ void l2_random_kernel(const uint4* __restrict__ buf, uint64_t n, uint
     out[tid] = acc;
 }
 
-// Random reads from a buffer far larger than L2, in the forms the update
-// kernel's step-record reads take. mode 0: one 16-byte load per thread with
-// the evict-first policy and the 64-byte L2 prefetch-size hint (the update
-// kernel's load_step); mode 1: the same load without the hint; mode 2: a
-// random 64-byte block per group of four lanes (four coalesced 16-byte
-// pieces, so the whole DRAM access is used). loads_per_thread independent
-// loads per thread, four in flight. Every index is below n (mulhi64 of a
-// 64-bit hash by n).
+// Random reads from a buffer far larger than L2, in the pattern of the
+// update and stress kernels on a large graph: the buffer is cut into 90
+// equal "paths" of 16-byte records; unit Q picks path p = Q mod 90 and, from
+// one Philox4x32-10 block of counter (Q / 90, 0, p, 0), two records i and j
+// uniform on that path (mulhi64 of a 64-bit word), read with the step-record
+// load (evict-first, 64-byte prefetch hint). mode 1 adds two random 8-byte
+// reads per unit from a node-sized array (88 MB, evict-last, L2-resident), as
+// an update's two point reads. Grid-stride over the units, one unit in
+// flight per thread. Every index is below its array's length.
 template <int MODE>
-__global__ void hbm_gather_kernel(const uint4* __restrict__ buf, uint64_t n, uint32_t loads_per_thread,
-                                  uint64_t salt, uint32_t* out) {
+__global__ void __launch_bounds__(256, 4) hbm_gather_kernel(const StepRec* __restrict__ buf, uint64_t per_path,
+                                                            const NodeRec* __restrict__ small, uint32_t n_small,
+                                                            uint64_t units, uint32_t* out) {
+    const uint64_t pol_stream = policy_evict_first(), pol_keep = policy_evict_last();
+    const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    const uint64_t pol = policy_evict_first();
     uint32_t acc = 0;
-    for (uint32_t r = 0; r < loads_per_thread; r += 4) {
-        uint4 v[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const uint64_t key = (MODE == 2 ? (tid >> 2) : tid) * 0x100000001B3ull + salt + r + k;
-            uint64_t idx;
-            if (MODE == 2) idx = mulhi64(splitmix(key), n >> 2) * 4 + (tid & 3);  // < n (n is a multiple of 4)
-            else idx = mulhi64(splitmix(key), n);                                 // < n
-            const uint4* q = buf + idx;
-            if (MODE == 0)
-                asm volatile("ld.global.cg.L2::cache_hint.L2::64B.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
-                             : "=r"(v[k].x), "=r"(v[k].y), "=r"(v[k].z), "=r"(v[k].w) : "l"(q), "l"(pol));
-            else
-                asm volatile("ld.global.cg.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
-                             : "=r"(v[k].x), "=r"(v[k].y), "=r"(v[k].z), "=r"(v[k].w) : "l"(q), "l"(pol));
+    for (uint64_t Q = tid; Q < units; Q += nthr) {
+        const uint32_t p = (uint32_t)(Q % kGatherPaths);
+        const uint64_t q = Q / kGatherPaths;
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), p, 0u), 0x5EEDu, 0u);
+        const uint64_t i = mulhi64((uint64_t)w.x | ((uint64_t)w.y << 32), per_path);
+        const uint64_t j = mulhi64(((uint64_t)w.w << 32) | w.z, per_path);
+        const StepRec a = load_step(buf + p * per_path + i, pol_stream, true);
+        const StepRec b = load_step(buf + p * per_path + j, pol_stream, true);
+        acc ^= a.nr ^ b.pos;
+        if (MODE == 1) {
+            const float2 va = load_point(small + (a.nr ^ w.z) % n_small, 0, pol_keep, true);
+            const float2 vb = load_point(small + (b.nr ^ w.w) % n_small, 1, pol_keep, true);
+            acc ^= __float_as_uint(va.x) ^ __float_as_uint(vb.y);
         }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) acc ^= v[k].x ^ v[k].w;
     }
     out[tid] = acc;
 }
@@ -112,27 +114,33 @@ extern "C" int pgsgd_hbm_gather_bandwidth(uint64_t bytes, uint32_t reps, int mod
     if (bytes < (1ull << 30) || bytes > (64ull << 30))
         return report_error(PGSGD_EINVAL, "bytes must be in [1 GiB, 64 GiB]");
     if (reps == 0 || reps > 100) return report_error(PGSGD_EINVAL, "reps must be in [1, 100]");
-    if (mode < 0 || mode > 2) return report_error(PGSGD_EINVAL, "mode must be 0, 1 or 2");
-    if (blocks_per_sm < 1 || blocks_per_sm > 8) return report_error(PGSGD_EINVAL, "blocks_per_sm must be in [1, 8]");
+    if (mode != 0 && mode != 1) return report_error(PGSGD_EINVAL, "mode must be 0 or 1");
+    if (blocks_per_sm < 1 || blocks_per_sm > 64) return report_error(PGSGD_EINVAL, "blocks_per_sm must be in [1, 64]");
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const uint64_t n = (bytes / 64) * 4;  // 16-byte records, a whole number of 64-byte blocks
+    const uint64_t per_path = bytes / 16 / kGatherPaths;  // records per path
+    const uint64_t n = per_path * kGatherPaths;
+    const uint32_t n_small = kGatherSmall;
     const int block = 256, grid = sms * blocks_per_sm;
-    const uint32_t loads_per_thread = 512;
-    uint4* buf = nullptr;
+    const uint64_t units = 4 * n;  // each record read about 8 times per launch
+    StepRec* buf = nullptr;
+    NodeRec* small = nullptr;
     uint32_t* out = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     auto cleanup = [&]() {
         cudaFree(buf);
+        cudaFree(small);
         cudaFree(out);
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
     };
-    cudaError_t e = cudaMalloc(&buf, n * 16);
+    cudaError_t e = cudaMalloc(&buf, n * sizeof(StepRec));
+    if (e == cudaSuccess) e = cudaMalloc(&small, (size_t)n_small * sizeof(NodeRec));
     if (e == cudaSuccess) e = cudaMalloc(&out, (size_t)grid * block * sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMemsetAsync(buf, 1, n * 16, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(buf, 1, n * sizeof(StepRec), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(small, 0, (size_t)n_small * sizeof(NodeRec), st);
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     if (e != cudaSuccess) {
@@ -143,10 +151,8 @@ extern "C" int pgsgd_hbm_gather_bandwidth(uint64_t bytes, uint32_t reps, int mod
     for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {  // pass 0 warms up
         e = cudaEventRecord(e0, st);
         for (uint32_t r = 0; r < reps && e == cudaSuccess; ++r) {
-            const uint64_t salt = 0x5851F42D4C957F2Dull * (pass * 1000ull + r + 1);
-            if (mode == 0) hbm_gather_kernel<0><<<grid, block, 0, st>>>(buf, n, loads_per_thread, salt, out);
-            else if (mode == 1) hbm_gather_kernel<1><<<grid, block, 0, st>>>(buf, n, loads_per_thread, salt, out);
-            else hbm_gather_kernel<2><<<grid, block, 0, st>>>(buf, n, loads_per_thread, salt, out);
+            if (mode == 0) hbm_gather_kernel<0><<<grid, block, 0, st>>>(buf, per_path, small, n_small, units, out);
+            else hbm_gather_kernel<1><<<grid, block, 0, st>>>(buf, per_path, small, n_small, units, out);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaEventRecord(e1, st);
@@ -155,11 +161,9 @@ extern "C" int pgsgd_hbm_gather_bandwidth(uint64_t bytes, uint32_t reps, int mod
     }
     cleanup();
     if (e != cudaSuccess) return report_error(PGSGD_ECUDA, "HBM gather probe: %s", cudaGetErrorString(e));
-    const double loads = (double)grid * block * loads_per_thread * reps / (mode == 2 ? 4.0 : 1.0);
-    *loads_per_s = loads / (ms * 1e-3);
+    *loads_per_s = 2.0 * (double)units * reps / (ms * 1e-3);  // the large buffer's random reads
     return PGSGD_OK;
 }
-
 extern "C" int pgsgd_l2_bandwidth(uint64_t bytes, uint32_t reps, int mode, double* gbs, void* cuda_stream) {
     if (!gbs) return report_error(PGSGD_EINVAL, "gbs is NULL");
     if (bytes < (1u << 20) || bytes > (1ull << 30)) return report_error(PGSGD_EINVAL, "bytes must be in [1 MiB, 1 GiB]");

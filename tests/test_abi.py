@@ -96,7 +96,7 @@ def test_l2_probe_rejects_bad_arguments_without_touching_the_gpu():
 def test_hbm_gather_probe_rejects_bad_arguments_without_touching_the_gpu():
     import paper_2409_00876_gb300 as pg
     from paper_2409_00876_gb300 import PgsgdError
-    for kw in [dict(bytes_=1 << 20), dict(bytes_=65 << 30), dict(reps=0), dict(reps=101), dict(mode=3),
-               dict(mode=-1), dict(blocks_per_sm=0), dict(blocks_per_sm=9)]:
+    for kw in [dict(bytes_=1 << 20), dict(bytes_=65 << 30), dict(reps=0), dict(reps=101), dict(mode=2),
+               dict(mode=-1), dict(blocks_per_sm=0), dict(blocks_per_sm=65)]:
         with pytest.raises(PgsgdError):
             pg.hbm_gather_rate(**kw)

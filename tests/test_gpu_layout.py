@@ -72,21 +72,26 @@ def test_tiny_layout_quality_matches_oracle_within_1_percent(pg):
     assert abs(got.mean() - ref.mean()) <= 0.01 * ref.mean(), (got.mean(), ref.mean())
 
 
-@pytest.mark.parametrize("name", ["mid", "chrom"])
+@pytest.mark.parametrize("name", ["mid", "mid_1000", "chrom"])
 def test_layout_stress_matches_oracle(pg, name):
-    """The GPU's lock-free layout reaches the oracle's quality. For every layout
-    seed the oracle recorded, the GPU lays the graph out under the same seed
-    (the same drawn pairs, applied concurrently). The mean stresses are
-    compared; the bar is the larger of 1 % of the oracle's mean and twice the
-    standard error that the seed-to-seed and run-to-run spread of both sides
-    implies. For the chromosome graph the oracle recorded one seed (each run
-    takes hours): the GPU's expected stress, estimated by five repeats, must be
-    within 1 % of the oracle's mean plus two standard errors of the
-    difference. The oracle's runs are draws of a lock-free process too; their
-    run-to-run variance is the measured one when the record holds repeats,
-    else taken to be that of one GPU run."""
+    """The GPU's lock-free layout reaches the oracle's quality (the 1 % target
+    on the sampled path stress, Eq. 2, under the same layout and stress
+    seeds). Every variance in the bar is measured, none assumed:
+
+    - records over several layout seeds (mid: 6 seeds at 100 samples per
+      step; mid_1000: 16 seeds at 1000): the GPU lays the graph out once per
+      seed; SE of the difference of the means from the two sides' measured
+      seed-to-seed spreads; bar max(1 %, 2 SE). mid_1000 must resolve the
+      target (2 SE <= 1 %): at 100 samples per step the heavy-tailed sample
+      set, not the layout, makes most of the spread, and ten times the
+      samples shrink it from about 7 % to about 1 % per layout;
+    - the chromosome graph (one seed, each oracle run takes hours): five GPU
+      repeats against the oracle's repeats of the same seed; SE from the
+      measured run-to-run spreads of both; bar max(1 %, 2 SE). It needs two
+      oracle runs at least, else the oracle's spread is unknown and the test
+      skips."""
     gold = _gold(name)
-    g = make_graph(name)
+    g = make_graph(gold.get("graph", name))
     fp = gold["fingerprint"]
     assert (g.n_nodes, g.n_paths, g.n_steps) == (fp["n_nodes"], fp["n_paths"], fp["n_steps"])
     per, sseed = gold["stress_samples_per_step"], gold["stress_seed"]
@@ -94,14 +99,15 @@ def test_layout_stress_matches_oracle(pg, name):
     seeds = [r["seed"] for r in gold["runs"]]
     if len(set(seeds)) > 1:
         got = np.array([_layout_stress(pg, g, sd, per, sseed)[0]["mean"] for sd in seeds])
-        se = np.sqrt(got.var(ddof=1) / len(got) + ref.var(ddof=1) / len(ref))
-        bar = max(0.01 * ref.mean(), 2 * se)
     else:
+        if len(ref) < 2:
+            pytest.skip(f"{name}: one oracle run; its run-to-run spread is not measured")
         got = np.array([_layout_stress(pg, g, seeds[0], per, sseed)[0]["mean"] for _ in range(5)])
-        v = got.var(ddof=1)
-        vo = ref.var(ddof=1) if len(ref) > 1 else v
-        bar = 0.01 * ref.mean() + 2 * np.sqrt(v / len(got) + vo / len(ref))
-    print(name, got, ref, abs(got.mean() - ref.mean()) / ref.mean(), bar / ref.mean())
+    se = np.sqrt(got.var(ddof=1) / len(got) + ref.var(ddof=1) / len(ref))
+    bar = max(0.01 * ref.mean(), 2 * se)
+    print(name, got, ref, (got.mean() - ref.mean()) / ref.mean(), 2 * se / ref.mean())
+    if name == "mid_1000":
+        assert 2 * se <= 0.01 * ref.mean(), (se, ref.mean())
     assert abs(got.mean() - ref.mean()) <= bar, (got, ref, bar)
     assert got.max() < 0.5 * gold["init_stress"]
 

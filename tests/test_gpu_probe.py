@@ -15,10 +15,9 @@ def test_l2_bandwidth_is_plausible():
 
 def test_hbm_random_read_rate_is_plausible():
     import paper_2409_00876_gb300 as pg
-    hint = pg.hbm_gather_rate(4 << 30, 2, 0)
-    plain = pg.hbm_gather_rate(4 << 30, 2, 1)
-    block = pg.hbm_gather_rate(4 << 30, 2, 2)
+    steps = pg.hbm_gather_rate(4 << 30, 2, 0)
+    with_nodes = pg.hbm_gather_rate(4 << 30, 2, 1)
     # every read costs at least one 32-byte sector of DRAM traffic, which cannot exceed
     # ~1.5x the copy peak; and a random read rate below 1e9/s would mean a broken probe
-    for r in (hint, plain, block):
-        assert 1e9 < r < 1.5 * 8e12 / 32, (hint, plain, block)
+    for r in (steps, with_nodes):
+        assert 1e9 < r < 1.5 * 8e12 / 32, (steps, with_nodes)

@@ -73,10 +73,12 @@ def _sparse_iteration(pg, g, drf, wm, srf, t=10, seed=3, **opts):
 
 @pytest.mark.parametrize("drf,wm,opts", [
     (1, 0, {}), (1, 1, {}), (2, 0, {}), (4, 1, {}), (8, 0, {}),
-    # the other compiled shapes of the plain update loop
-    (1, 0, dict(pipeline=1)), (1, 0, dict(pipeline=1, updates_per_thread=2)),
-    (1, 0, dict(updates_per_thread=2)), (1, 0, dict(updates_per_thread=4)), (1, 0, dict(min_blocks=1)),
-    (1, 0, dict(min_blocks=6)), (1, 0, dict(updates_per_thread=2, min_blocks=1)), (1, 1, dict(updates_per_thread=4)),
+    # the other compiled shapes of the plain update loop (the default is the pipelined one at 2)
+    (1, 0, dict(pipeline=0, updates_per_thread=1)), (1, 0, dict(pipeline=1, updates_per_thread=1)),
+    (1, 0, dict(pipeline=1, updates_per_thread=2)),
+    (1, 0, dict(pipeline=0, min_blocks=6)), (1, 0, dict(pipeline=0, updates_per_thread=2, min_blocks=1)),
+    (1, 0, dict(pipeline=0, updates_per_thread=2)), (1, 0, dict(pipeline=0, updates_per_thread=4)),
+    (1, 0, dict(pipeline=0, min_blocks=1)), (1, 1, dict(updates_per_thread=4)),
     # the asynchronous step-record loop: one block of 256 threads, so every thread
     # runs 4 updates and cycles through its slots
     (1, 0, dict(async_depth=2, max_concurrent=256)), (1, 0, dict(async_depth=3, max_concurrent=256)),
@@ -128,9 +130,14 @@ def test_variant_options_are_checked(pg):
             G.set_option(name, bad)
     G.set_coords(g.init_xy)
     G.set_option("drf", 2)
-    G.set_option("pipeline", 1)
+    G.set_option("pipeline", 1)  # set by hand: an error, since data reuse runs the plain loop
     with pytest.raises(PgsgdError, match="pipeline"):
         G.layout(T)
+    G.set_option("pipeline", -1)  # automatic: the plain loop under data reuse
+    G.layout(T, iter_end=1)
+    for name, bad in [("pipeline", 2), ("pipeline", -2), ("updates_per_thread", 3)]:
+        with pytest.raises(PgsgdError):
+            G.set_option(name, bad)
     G.set_option("pipeline", 0)
     G.set_option("drf", 1)
     with pytest.raises(PgsgdError, match="reuse is off"):
