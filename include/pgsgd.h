@@ -151,8 +151,10 @@ typedef enum pgsgd_option {
      * (default), D in {2, 4, 8} samples' step-record reads in flight per
      * thread. Same samples and sums. */
     PGSGD_OPT_STRESS_ASYNC = 20,
-    /* Grid of the sampled-stress kernel: 0 = 8 blocks per SM (default);
-     * W in 1..8 = W whole waves of the blocks that fit on the GPU at once. */
+    /* Grid of the sampled-stress kernel: W in 1..8 = W whole waves of the
+     * blocks that fit on the GPU at once (default 1: every block slot stays
+     * busy to the end; 2.09 s against 2.15 s for the chromosome graph's
+     * 4.7e10 samples), 0 = 8 blocks per SM (2.67 waves at 3 resident). */
     PGSGD_OPT_STRESS_WAVES = 21
 } pgsgd_option;
 

@@ -162,7 +162,7 @@ struct pgsgd_graph {
     int warp_merge = 0;
     int async_depth = 0;  // cp.async step-record ring depth of the update kernel (0 = off)
     int stress_async = 0; // the same for the sampled-stress kernel
-    int stress_waves = 0; // stress grid: whole waves of resident blocks (0 = the former fixed grid)
+    int stress_waves = 1; // stress grid: whole waves of resident blocks (0 = 8 blocks per SM)
     int drf = 1;          // data reuse factor
     int srf = 1;          // step reduction factor
 
