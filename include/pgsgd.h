@@ -87,7 +87,8 @@ typedef enum pgsgd_option {
     /* Register budget of the update kernel: the number of resident 256-thread
      * blocks per SM its registers must allow (1 = compiler's choice; the
      * compiled variants are 1, 4, 6 for 1 update per thread, 1, 3, 4 for 2
-     * and 1, 2, 3 for 4; the pipelined loop: 1, 3 for 1 and 1, 2 for 2).
+     * and 1, 2, 3 for 4; the pipelined loop: 1, 3 for 1, 1, 2, 3 for 2 and
+     * 1, 2 for 4).
      * Default 0 = automatic: for the plain loop 4 at 1 update per thread and
      * 3 at 2 (no spills); for the pipelined loop 2 at 2 updates per thread
      * (98 registers, no spills); else 1. */
@@ -118,7 +119,7 @@ typedef enum pgsgd_option {
     /* 1 = software-pipelined update loop: each thread issues a trip's
      * step-record loads, then draws the next trip's pairs while they are in
      * flight (same draws and moves; compiled for updates per thread / min
-     * blocks 1/1, 1/3, 2/1, 2/2 and 4/1). Default -1 = automatic: the
+     * blocks 1/1, 1/3, 2/1, 2/2, 2/3, 4/1 and 4/2). Default -1 = automatic: the
      * pipelined loop for the plain method, the plain loop under warp
      * merging, data reuse or PGSGD_OPT_ASYNC_DEPTH, which need it (setting 1
      * with them is an error). */

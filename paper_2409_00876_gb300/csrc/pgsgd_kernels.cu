@@ -787,7 +787,9 @@ cudaError_t launch_update(const UpdateLaunch& L, cudaStream_t st) {
             case 13: return launch_update_t<1, 3, true>(L, st);
             case 21: return launch_update_t<2, 1, true>(L, st);
             case 22: return launch_update_t<2, 2, true>(L, st);
+            case 23: return launch_update_t<2, 3, true>(L, st);
             case 41: return launch_update_t<4, 1, true>(L, st);
+            case 42: return launch_update_t<4, 2, true>(L, st);
             default: return cudaErrorInvalidValue;
         }
     }

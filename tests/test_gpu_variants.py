@@ -75,7 +75,8 @@ def _sparse_iteration(pg, g, drf, wm, srf, t=10, seed=3, **opts):
     (1, 0, {}), (1, 1, {}), (2, 0, {}), (4, 1, {}), (8, 0, {}),
     # the other compiled shapes of the plain update loop (the default is the pipelined one at 2)
     (1, 0, dict(pipeline=0, updates_per_thread=1)), (1, 0, dict(pipeline=1, updates_per_thread=1)),
-    (1, 0, dict(pipeline=1, updates_per_thread=2)),
+    (1, 0, dict(pipeline=1, updates_per_thread=2)), (1, 0, dict(pipeline=1, updates_per_thread=2, min_blocks=3)),
+    (1, 0, dict(pipeline=1, updates_per_thread=4, min_blocks=2)),
     (1, 0, dict(pipeline=0, min_blocks=6)), (1, 0, dict(pipeline=0, updates_per_thread=2, min_blocks=1)),
     (1, 0, dict(pipeline=0, updates_per_thread=2)), (1, 0, dict(pipeline=0, updates_per_thread=4)),
     (1, 0, dict(pipeline=0, min_blocks=1)), (1, 1, dict(updates_per_thread=4)),
