@@ -268,9 +268,10 @@ def cpu_baseline(g, budget_s=12.0, warmup=False):
             "sample": f"bounded samples of the same graph and seed, FP64, {threads} threads: {desc}"}
 
 
-def cpu_full_layouts(names=("tiny",)):
+def cpu_full_layouts(names=("tiny",), single_thread=("tiny",)):
     """Whole oracle layouts (30 iterations x 10 x S updates) timed on the host:
-    one thread (the sequential definition) and all cores (Hogwild!)."""
+    all cores (Hogwild!), and one thread (the sequential definition) for the
+    workloads in single_thread."""
     import oracle as O
     from synth import make_graph
     threads = os.cpu_count() or 1
@@ -279,7 +280,7 @@ def cpu_full_layouts(names=("tiny",)):
         g = make_graph(name)
         eta = O.eta_schedule(ITERS, O.default_eta_max(g))
         row = {"updates": ITERS * 10 * g.n_steps}
-        for k in sorted({1, threads}):
+        for k in sorted({1, threads} if name in single_thread else {threads}):
             t0 = time.perf_counter()
             O.layout(g, g.init_xy, T=ITERS, eta=eta, theta=THETA, seed=SEED, n_threads=k)
             dt = time.perf_counter() - t0
@@ -903,8 +904,9 @@ def main(argv=None):
     ap.add_argument("--skip-gather", action="store_true", help="skip the HBM random-read probe (profiling runs)")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-budget", type=float, default=10.0)
-    ap.add_argument("--cpu-full", nargs="*", default=["tiny"], choices=["tiny", "mid"],
-                    help="workloads whose whole oracle layout is timed on the host (1 thread and all cores)")
+    ap.add_argument("--cpu-full", nargs="*", default=["tiny", "mid"], choices=["tiny", "mid"],
+                    help="workloads whose whole oracle layout is timed on the host (all cores; tiny also on 1 "
+                         "thread: the 200 k-node graph takes about 10 minutes on one)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the data-reuse, batched and differentiable forms (chromosome run) or the "
                          "schedule comparison (batch runs)")
