@@ -87,3 +87,30 @@ def test_traffic_record_belongs_to_the_current_update_kernel():
     per_update = (rec["dram_bytes_read_per_launch"] + rec["dram_bytes_write_per_launch"]) / rec["updates_per_launch"]
     assert rec["dram_bytes_per_update"] == pytest.approx(per_update, abs=0.01)
     assert rec["updates_per_launch"] == 10 * 62_504_258  # 10 x S of the profiling graph
+
+
+def test_phase_clocks_take_the_samples_inside_the_windows():
+    from datetime import datetime
+    t0 = datetime(2026, 12, 4, 6, 0, 0).timestamp()
+
+    def line(sm, dt):
+        ts = datetime.fromtimestamp(t0 + dt).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        return _sample(sm) + ", " + ts
+
+    lines = [line(1500, 0.1), line(2000, 1.1), line(1990, 1.3), line(1700, 2.5), line(1980, 3.2)]
+    c = bench.clocks_in_windows(lines, [(t0 + 1.0, t0 + 1.5), (t0 + 3.0, t0 + 3.5)])
+    assert c["samples"] == 3 and c["sm_mhz_median"] == 1990 and c["sm_mhz_min"] == 1980
+    assert bench.clocks_in_windows(lines, [(t0 + 5, t0 + 6)])["samples"] == 0
+    # the summary over all samples still reads lines that carry the timestamp
+    assert bench.summarize_clocks(lines)["samples"] == 5
+
+
+def test_random_gather_fields_of_the_roofline():
+    gather = {"reads_per_s": 48e9, "reads_per_s_with_node_reads": 37e9, "gbs_as_32B_sectors": 1536.0,
+              "gbs_as_64B_accesses": 3072.0, "pattern": "p"}
+    ref = {"kernel": "stress_kernel", "units_per_s": 22e9}
+    r = bench.roofline_for("chrom", 4100.0, 6785.2, "measured", None, 218.6, gather, 42.9e9, ref, 21.4e9)
+    assert r["random_gather_gbs"] == 1536.0
+    assert r["frac_of_random_gather"] == pytest.approx(42.9 / 48)
+    assert r["gather_reference"]["update_frac"] == pytest.approx(21.4 / 22)
+    assert r["frac"] == pytest.approx(4100.0 / 6785.2)
