@@ -32,11 +32,12 @@ typedef enum pgsgd_batch_option {
      *     every graph gets `lanes` blocks, lane k runs the graph's chunks
      *     k, k + lanes, ...;
      * 1 = one persistent launch for all iterations: blocks claim chunks from
-     *     per-graph queues (largest graph first); the block that completes a
-     *     graph's last chunk of an iteration opens its next iteration, so
-     *     graphs advance independently. Synchronous: the call waits for the
-     *     kernel and returns PGSGD_ETIMEOUT if a block found no claimable
-     *     work for PGSGD_BOPT_TIMEOUT_MS (a stuck queue);
+     *     per-graph queues (largest graph first; a block's first warp claims
+     *     its next chunk while the other warps finish the current one); the
+     *     block that completes a graph's last chunk of an iteration opens its
+     *     next iteration, so graphs advance independently. Synchronous: the
+     *     call waits for the kernel and returns PGSGD_ETIMEOUT if a block
+     *     found no claimable work for PGSGD_BOPT_TIMEOUT_MS (a stuck queue);
      * 2 = one launch per graph per iteration (the comparison point). */
     PGSGD_BOPT_MODE = 1,
     /* Modes 0 and 2: 1 (default) = capture the layout's launches once into a

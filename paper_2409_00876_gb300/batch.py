@@ -192,7 +192,7 @@ def autotune(b, xy, seeds=1, iter_max=30, theta=0.99, window=None, repeats=1, sp
     if window is None:
         window = (iter_max // 2 - 1, iter_max // 2 + 1)
     space = space or dict(mode=[0, 1], pipeline=[0, 1], updates_per_thread=[2, 1, 4], block=[256, 128],
-                          chunk=[16384, 4096, 65536])
+                          chunk=[16384, 4096, 32768, 65536])
     keys = list(space)
     cur = {k: b.get_option(k) for k in keys}
     for k in keys:

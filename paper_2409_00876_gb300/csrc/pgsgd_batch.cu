@@ -278,8 +278,16 @@ __device__ __forceinline__ void complete_chunk(const BatchLaunch& L, const Batch
     }
 }
 
+// A register budget of 3 resident blocks per SM (2 at 4 updates per thread)
+// as the lane kernels have; without it the queue logic took the kernel to
+// 102-124 registers and 2 blocks per SM.
+// Warp 0 claims the block's next chunk while the other warps finish their
+// share of the current one, so a claim's scan of the queues costs no time
+// between chunks; the current chunk is completed (and its graph's next
+// iteration possibly opened) after the block's barrier, then the claimed
+// command is published for the next trip.
 template <int UPT, bool PIPE>
-__global__ void __launch_bounds__(256) batch_persistent_kernel(BatchLaunch L, uint32_t max_paths, BatchQueues Q) {
+__global__ void __launch_bounds__(256, UPT == 4 ? 2 : 3) batch_persistent_kernel(BatchLaunch L, uint32_t max_paths, BatchQueues Q) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ ZipfConsts zc;
     __shared__ uint32_t s_cmd[4];  // status, rank, iteration, chunk
@@ -290,33 +298,39 @@ __global__ void __launch_bounds__(256) batch_persistent_kernel(BatchLaunch L, ui
     BatchGraph G{};
     bool waiting = false;
     uint64_t wait_start = 0;
-    for (;;) {
-        if (threadIdx.x < 32) {
-            uint32_t r = 0, t = 0, c = 0;
-            int st = claim_chunk(L, Q, r, t, c);
-            if (threadIdx.x == 0) {
-                if (st == 1) {
-                    // nothing claimable: every open chunk is held by a running
-                    // block, so this ends unless a queue is stuck; bounded
-                    const uint64_t now = global_ns();
-                    if (!waiting) {
-                        waiting = true;
-                        wait_start = now;
-                    } else if (now - wait_start > L.timeout_ns) {
-                        atomicOr(Q.err, BERR_TIMEOUT);
-                        st = 3;
-                    }
-                } else {
-                    waiting = false;
+    // warp 0: one claim; lane 0 (thread 0) keeps the bounded-wait bookkeeping
+    auto claim = [&](uint32_t (&cmd)[4]) {
+        uint32_t r = 0, t = 0, c = 0;
+        int st = claim_chunk(L, Q, r, t, c);
+        if (threadIdx.x == 0) {
+            if (st == 1) {
+                // nothing claimable: every open chunk is held by a running
+                // block, so this ends unless a queue is stuck; bounded
+                const uint64_t now = global_ns();
+                if (!waiting) {
+                    waiting = true;
+                    wait_start = now;
+                } else if (now - wait_start > L.timeout_ns) {
+                    atomicOr(Q.err, BERR_TIMEOUT);
+                    st = 3;
                 }
-                s_cmd[0] = (uint32_t)st;
-                s_cmd[1] = r;
-                s_cmd[2] = t;
-                s_cmd[3] = c;
+            } else {
+                waiting = false;
             }
-            if (__shfl_sync(0xffffffffu, st, 0) == 1) __nanosleep(2000);
         }
-        __syncthreads();
+        cmd[0] = (uint32_t)st;
+        cmd[1] = r;
+        cmd[2] = t;
+        cmd[3] = c;
+    };
+    if (threadIdx.x < 32) {
+        uint32_t cmd[4];
+        claim(cmd);
+        if (threadIdx.x == 0)
+            for (int k = 0; k < 4; ++k) s_cmd[k] = cmd[k];
+    }
+    __syncthreads();
+    for (;;) {
         const uint32_t st = s_cmd[0], r = s_cmd[1], t = s_cmd[2], c = s_cmd[3];
         if (st >= 2) break;
         if (st == 0) {
@@ -328,8 +342,16 @@ __global__ void __launch_bounds__(256) batch_persistent_kernel(BatchLaunch L, ui
             }
             run_chunk<UPT, PIPE>(L, G, r, s, zc, t, c, pol_stream, pol_keep);
             __threadfence();
-            __syncthreads();
-            if (threadIdx.x == 0) complete_chunk(L, Q, r, t);
+        }
+        uint32_t next[4] = {0u, 0u, 0u, 0u};
+        if (threadIdx.x < 32) {
+            claim(next);
+            if (next[0] == 1) __nanosleep(2000);
+        }
+        __syncthreads();  // every thread's share of the current chunk is done and fenced; all read s_cmd
+        if (threadIdx.x == 0) {
+            if (st == 0) complete_chunk(L, Q, r, t);
+            for (int k = 0; k < 4; ++k) s_cmd[k] = next[k];
         }
         __syncthreads();
     }
