@@ -81,8 +81,12 @@ typedef enum pgsgd_option {
     PGSGD_OPT_TIMING = 8,
     /* Concurrency cap: the update kernel's grid is shrunk so that at most this
      * many updates are in flight at once (0 = no cap; -1, the default,
-     * = max(2048, n_nodes / 2)). Small graphs under a full GB300 grid would
-     * otherwise see many simultaneous updates per node. */
+     * = max(2048, n_nodes / 4)). Small graphs under a full GB300 grid would
+     * otherwise see many simultaneous updates per node: on the 200 k-node
+     * graph a cap of n_nodes / 2 left the sampled stress 1.1 % above the
+     * oracle's (16 seeds, paired), n_nodes / 4 0.4 %, at 1.8x the layout
+     * time; on the 5.5 M-node graph the resident threads, not the cap, bound
+     * the updates in flight. */
     PGSGD_OPT_MAX_CONCURRENT = 9,
     /* Register budget of the update kernel: the number of resident 256-thread
      * blocks per SM its registers must allow (1 = compiler's choice; the

@@ -52,7 +52,7 @@ typedef enum pgsgd_batch_option {
     PGSGD_BOPT_CHUNK = 5,
     /* Per-graph cap on updates in flight: graph g runs at most
      * max(1, cap / (block * updates per thread)) chunks at once.
-     * -1 (default) = max(2048, nodes of g / 2), the single-graph rule;
+     * -1 (default) = max(2048, nodes of g / 4), the single-graph rule;
      * 0 = no cap. */
     PGSGD_BOPT_MAX_CONCURRENT = 6,
     /* Updates per iteration of graph g = this value times its steps

@@ -598,7 +598,7 @@ int pgsgd_layout(pgsgd_graph* g, uint32_t iter_max, const double* eta, double et
     const int per_sm = g->blocks_per_sm;
     int grid = g->sm_count * per_sm;
     int64_t cap = g->max_concurrent;
-    if (cap == -1) cap = std::max<int64_t>(2048, (int64_t)g->n_nodes / 2);
+    if (cap == -1) cap = std::max<int64_t>(2048, (int64_t)g->n_nodes / 4);
     if (cap > 0) {
         // the cap counts updates: a thread keeps upt updates, or one selection of drf updates, in flight
         const int64_t per_block = (int64_t)g->block * (g->drf > 1 ? g->drf : upt);

@@ -19,7 +19,7 @@
 //           end in PGSGD_ETIMEOUT;
 //   mode 2  the comparison point: per iteration, one launch per graph.
 // Per graph at most `max_active` chunks are in flight, i.e. at most
-// max_active * block * upt updates at once (default cap max(2048, V_g / 2)
+// max_active * block * upt updates at once (default cap max(2048, V_g / 4)
 // updates, the single-graph kernel's rule), so small graphs see no more
 // simultaneous updates than when laid out alone.
 #include <algorithm>
@@ -635,7 +635,7 @@ int make_plan(uint32_t G, const uint64_t* n_updates, const uint64_t* n_nodes, in
             active = nc;
         } else {
             const uint64_t cap = max_concurrent > 0 ? (uint64_t)max_concurrent
-                                                    : std::max<uint64_t>(2048, n_nodes[gi] / 2);
+                                                    : std::max<uint64_t>(2048, n_nodes[gi] / 4);
             active = std::max<uint64_t>(1, cap / per_block);
         }
         lanes[gi] = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(active, 1), std::max<uint64_t>(nc, 1));

@@ -51,8 +51,8 @@ def test_plan_orders_by_work_and_caps_lanes():
     # most updates first, ties by graph index
     assert list(r2g) == [4, 2, 3, 0, 1]
     np.testing.assert_array_equal(nch, [1, 0, 5, 5, 70])
-    # cap = max(2048, V / 2) updates in flight = cap // 512 chunks, at most the chunks there are
-    caps = np.maximum(2048, nn // 2) // 512
+    # cap = max(2048, V / 4) updates in flight = cap // 512 chunks, at most the chunks there are
+    caps = np.maximum(2048, nn // 4) // 512
     np.testing.assert_array_equal(lanes, np.where(nch == 0, 0, np.minimum(np.maximum(caps, 1), nch)))
 
 
@@ -61,7 +61,7 @@ def test_plan_options_change_lanes():
     nn = np.array([200_000], np.uint64)
     _, nch, lanes = _plan(nu, nn, block=128, updates_per_thread=4, chunk=4096)
     assert nch[0] == -(-10_000_000 // 4096)
-    assert lanes[0] == 100_000 // 512
+    assert lanes[0] == 50_000 // 512  # cap V / 4 = 50,000 updates over 128 x 4 per lane
     _, _, lanes0 = _plan(nu, nn, chunk=4096, max_concurrent=0)
     assert lanes0[0] == nch[0]  # no cap: every chunk may run at once
     _, _, lanes1 = _plan(nu, nn, chunk=4096, max_concurrent=100)

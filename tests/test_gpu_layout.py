@@ -76,15 +76,17 @@ def test_tiny_layout_quality_matches_oracle_within_1_percent(pg):
 def test_layout_stress_matches_oracle(pg, name):
     """The GPU's lock-free layout reaches the oracle's quality (the 1 % target
     on the sampled path stress, Eq. 2, under the same layout and stress
-    seeds). Every variance in the bar is measured, none assumed:
+    seeds; reading R28). Every variance in the bar is measured, none assumed:
 
     - records over several layout seeds (mid: 6 seeds at 100 samples per
       step; mid_1000: 16 seeds at 1000): the GPU lays the graph out once per
-      seed; SE of the difference of the means from the two sides' measured
-      seed-to-seed spreads; bar max(1 %, 2 SE). mid_1000 must resolve the
-      target (2 SE <= 1 %): at 100 samples per step the heavy-tailed sample
-      set, not the layout, makes most of the spread, and ten times the
-      samples shrink it from about 7 % to about 1 % per layout;
+      seed, and the comparison is paired by seed, since a seed's draws are the
+      same on both sides and fix most of its layout's stress (the per-seed
+      stresses of the two sides correlate at 0.96 on mid_1000): the mean
+      difference over seeds, SE from the spread of the per-seed differences;
+      bar max(1 %, 2 SE). mid_1000 must resolve the target (2 SE <= 1 %);
+      at 100 samples per step the heavy-tailed sample set makes most of the
+      spread (reading R29);
     - the chromosome graph (one seed, each oracle run takes hours): five GPU
       repeats against the oracle's repeats of the same seed; SE from the
       measured run-to-run spreads of both; bar max(1 %, 2 SE). It needs two
@@ -98,12 +100,15 @@ def test_layout_stress_matches_oracle(pg, name):
     ref = np.array([r["stress"] for r in gold["runs"]])
     seeds = [r["seed"] for r in gold["runs"]]
     if len(set(seeds)) > 1:
+        assert len(set(seeds)) == len(seeds)
         got = np.array([_layout_stress(pg, g, sd, per, sseed)[0]["mean"] for sd in seeds])
+        d = got - ref
+        se = d.std(ddof=1) / np.sqrt(len(d))
     else:
         if len(ref) < 2:
             pytest.skip(f"{name}: one oracle run; its run-to-run spread is not measured")
         got = np.array([_layout_stress(pg, g, seeds[0], per, sseed)[0]["mean"] for _ in range(5)])
-    se = np.sqrt(got.var(ddof=1) / len(got) + ref.var(ddof=1) / len(ref))
+        se = np.sqrt(got.var(ddof=1) / len(got) + ref.var(ddof=1) / len(ref))
     bar = max(0.01 * ref.mean(), 2 * se)
     print(name, got, ref, (got.mean() - ref.mean()) / ref.mean(), 2 * se / ref.mean())
     if name == "mid_1000":
