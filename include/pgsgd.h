@@ -80,7 +80,8 @@ typedef enum pgsgd_option {
      * launching stream; read them with pgsgd_timing_read. Default 0. */
     PGSGD_OPT_TIMING = 8,
     /* Concurrency cap: the update kernel's grid is shrunk so that at most this
-     * many updates are in flight at once (0 = no cap; -1, the default,
+     * many updates are in flight at once, where the resident blocks would
+     * otherwise hold more (0 = no cap; -1, the default,
      * = max(2048, n_nodes / 4)). Small graphs under a full GB300 grid would
      * otherwise see many simultaneous updates per node: on the 200 k-node
      * graph a cap of n_nodes / 2 left the sampled stress 1.1 % above the

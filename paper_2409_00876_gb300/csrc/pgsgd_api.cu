@@ -594,23 +594,11 @@ int pgsgd_layout(pgsgd_graph* g, uint32_t iter_max, const double* eta, double et
     const uint64_t N_full = (uint64_t)g->updates_per_step * g->n_steps;
     const uint64_t N = (N_full + (uint64_t)g->srf - 1) / (uint64_t)g->srf;
     const uint64_t updates_per_launch = N * (uint64_t)g->drf;
-    // grid: a multiple of the SM count, capped by the concurrency limit
-    const int per_sm = g->blocks_per_sm;
-    int grid = g->sm_count * per_sm;
-    int64_t cap = g->max_concurrent;
-    if (cap == -1) cap = std::max<int64_t>(2048, (int64_t)g->n_nodes / 4);
-    if (cap > 0) {
-        // the cap counts updates: a thread keeps upt updates, or one selection of drf updates, in flight
-        const int64_t per_block = (int64_t)g->block * (g->drf > 1 ? g->drf : upt);
-        const int64_t gmax = std::max<int64_t>(1, cap / per_block);
-        if (gmax < grid) grid = (int)gmax;
-    }
     UpdateLaunch L;
     L.nodes = g->d_nodes;
     L.u_begin = 0;
     L.n_updates = N;
     L.block = g->block;
-    L.grid = grid;
     L.upt = upt;
     // automatic register budget for the plain loop: 4 resident blocks per SM
     // at 1 update per thread, 3 at 2 (no spills either way), else the
@@ -624,6 +612,23 @@ int pgsgd_layout(pgsgd_graph* g, uint32_t iter_max, const double* eta, double et
     L.wm = g->warp_merge != 0;
     L.drf = g->drf;
     L.atomic = g->atomic != 0;
+    L.s = sampler_args(g, iter_max, iter_begin, th, seed);
+    // grid: a multiple of the SM count; the concurrency cap bounds the updates
+    // in flight at once, so it shrinks the grid only where it is below what
+    // the resident blocks hold (a large graph keeps the full grid, whose
+    // resident blocks hold fewer updates than the cap)
+    int grid = g->sm_count * g->blocks_per_sm;
+    int64_t cap = g->max_concurrent;
+    if (cap == -1) cap = std::max<int64_t>(2048, (int64_t)g->n_nodes / 4);
+    if (cap > 0) {
+        // the cap counts updates: a thread keeps upt updates, or one selection of drf updates, in flight
+        const int64_t per_block = (int64_t)g->block * (g->drf > 1 ? g->drf : upt);
+        const int64_t gmax = std::max<int64_t>(1, cap / per_block);
+        const int nb = update_blocks_per_sm(L);
+        const int64_t resident = (int64_t)nb * g->sm_count;
+        if (gmax < grid && (nb <= 0 || gmax < resident)) grid = (int)gmax;
+    }
+    L.grid = grid;
     if (g->l2_fetch) CK(cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, g->l2_fetch), "L2 fetch limit");
     for (uint32_t t = iter_begin; t < iter_end; ++t) {
         L.s = sampler_args(g, iter_max, t, th, seed);

@@ -86,6 +86,7 @@ cudaError_t launch_refresh_anchors(StepRec* steps, const int32_t* anchor, uint64
 cudaError_t launch_zipf_setup(const uint64_t* path_off, uint32_t n_paths, float theta, float* zipf_B,
                               float* zipf_T, cudaStream_t st);
 cudaError_t launch_update(const UpdateLaunch& L, cudaStream_t st);
+int update_blocks_per_sm(const UpdateLaunch& L);  // resident blocks of the kernel L selects (0 on error)
 cudaError_t launch_debug_sample_reuse(const SamplerArgs& s, uint32_t R, uint64_t n_sel, uint64_t q_begin,
                                      uint64_t count, void* out, int sm_count, cudaStream_t st);
 cudaError_t launch_debug_sample(const SamplerArgs& s, uint64_t u_begin, uint64_t count, void* out,

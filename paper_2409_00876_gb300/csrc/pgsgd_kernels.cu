@@ -720,91 +720,93 @@ cudaError_t launch_zipf_setup(const uint64_t* path_off, uint32_t n_paths, float 
     return cudaGetLastError();
 }
 
-template <int UPT, int MINB, bool PIPE = false>
-static cudaError_t launch_update_t(const UpdateLaunch& L, cudaStream_t st) {
-    const size_t smem = update_smem_bytes(L.s.n_paths, L.s.n_guide);
-    cudaError_t e = cudaFuncSetAttribute(update_kernel<UPT, MINB, PIPE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    update_kernel<UPT, MINB, PIPE><<<L.grid, L.block, smem, st>>>(L);
-    return cudaGetLastError();
-}
+// The update kernel an UpdateLaunch selects, with its dynamic shared memory.
+struct UpdateKernelChoice {
+    const void* fn;
+    size_t smem;
+};
 
-// UPT = updates in flight per thread; MINB = resident 256-thread blocks per
-// SM the register allocation must allow (1 = unconstrained).
 template <class K>
-static cudaError_t launch_with_smem(K kernel, const UpdateLaunch& L, cudaStream_t st) {
+static UpdateKernelChoice pick(K kernel, size_t smem) {
+    return UpdateKernelChoice{reinterpret_cast<const void*>(kernel), smem};
+}
+
+static cudaError_t choose_update_kernel(const UpdateLaunch& L, UpdateKernelChoice* c) {
     const size_t smem = update_smem_bytes(L.s.n_paths, L.s.n_guide);
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kernel<<<L.grid, L.block, smem, st>>>(L);
-    return cudaGetLastError();
-}
-
-template <int D, int MINB>
-static cudaError_t launch_update_async_t(const UpdateLaunch& L, cudaStream_t st) {
-    const size_t smem = async_slots_offset(L.s.n_paths, L.s.n_guide) + (size_t)D * 2 * L.block * sizeof(StepRec);
-    cudaError_t e = cudaFuncSetAttribute(update_kernel_async<D, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    update_kernel_async<D, MINB><<<L.grid, L.block, smem, st>>>(L);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_update(const UpdateLaunch& L, cudaStream_t st) {
-    if (L.n_updates == 0) return cudaSuccess;
     if (L.async_depth > 0) {
+        const size_t sa = async_slots_offset(L.s.n_paths, L.s.n_guide) +
+                          (size_t)L.async_depth * 2 * L.block * sizeof(StepRec);
         switch (L.async_depth * 10 + L.minb) {
-            case 24: return launch_update_async_t<2, 4>(L, st);
-            case 34: return launch_update_async_t<3, 4>(L, st);
-            case 44: return launch_update_async_t<4, 4>(L, st);
-            case 45: return launch_update_async_t<4, 5>(L, st);
-            case 64: return launch_update_async_t<6, 4>(L, st);
-            case 84: return launch_update_async_t<8, 4>(L, st);
-            case 43: return launch_update_async_t<4, 3>(L, st);
+            case 24: *c = pick(update_kernel_async<2, 4>, sa); return cudaSuccess;
+            case 34: *c = pick(update_kernel_async<3, 4>, sa); return cudaSuccess;
+            case 44: *c = pick(update_kernel_async<4, 4>, sa); return cudaSuccess;
+            case 45: *c = pick(update_kernel_async<4, 5>, sa); return cudaSuccess;
+            case 64: *c = pick(update_kernel_async<6, 4>, sa); return cudaSuccess;
+            case 84: *c = pick(update_kernel_async<8, 4>, sa); return cudaSuccess;
+            case 43: *c = pick(update_kernel_async<4, 3>, sa); return cudaSuccess;
             default: return cudaErrorInvalidValue;
         }
     }
     if (L.drf > 1) {
         switch (L.drf) {
-            case 2: return launch_with_smem(update_reuse_kernel<2>, L, st);
-            case 4: return launch_with_smem(update_reuse_kernel<4>, L, st);
-            case 8: return launch_with_smem(update_reuse_kernel<8>, L, st);
+            case 2: *c = pick(update_reuse_kernel<2>, smem); return cudaSuccess;
+            case 4: *c = pick(update_reuse_kernel<4>, smem); return cudaSuccess;
+            case 8: *c = pick(update_reuse_kernel<8>, smem); return cudaSuccess;
             default: return cudaErrorInvalidValue;
         }
     }
     if (L.wm) {
         switch (L.upt) {
-            case 1: return launch_with_smem(update_kernel_wm<1>, L, st);
-            case 2: return launch_with_smem(update_kernel_wm<2>, L, st);
-            case 4: return launch_with_smem(update_kernel_wm<4>, L, st);
+            case 1: *c = pick(update_kernel_wm<1>, smem); return cudaSuccess;
+            case 2: *c = pick(update_kernel_wm<2>, smem); return cudaSuccess;
+            case 4: *c = pick(update_kernel_wm<4>, smem); return cudaSuccess;
             default: return cudaErrorInvalidValue;
         }
     }
     if (L.pipeline) {
         switch (L.upt * 10 + L.minb) {
-            case 11: return launch_update_t<1, 1, true>(L, st);
-            case 13: return launch_update_t<1, 3, true>(L, st);
-            case 21: return launch_update_t<2, 1, true>(L, st);
-            case 22: return launch_update_t<2, 2, true>(L, st);
-            case 23: return launch_update_t<2, 3, true>(L, st);
-            case 41: return launch_update_t<4, 1, true>(L, st);
-            case 42: return launch_update_t<4, 2, true>(L, st);
+            case 11: *c = pick(update_kernel<1, 1, true>, smem); return cudaSuccess;
+            case 13: *c = pick(update_kernel<1, 3, true>, smem); return cudaSuccess;
+            case 21: *c = pick(update_kernel<2, 1, true>, smem); return cudaSuccess;
+            case 22: *c = pick(update_kernel<2, 2, true>, smem); return cudaSuccess;
+            case 23: *c = pick(update_kernel<2, 3, true>, smem); return cudaSuccess;
+            case 41: *c = pick(update_kernel<4, 1, true>, smem); return cudaSuccess;
+            case 42: *c = pick(update_kernel<4, 2, true>, smem); return cudaSuccess;
             default: return cudaErrorInvalidValue;
         }
     }
     switch (L.upt * 10 + L.minb) {
-        case 11: return launch_update_t<1, 1>(L, st);
-        case 14: return launch_update_t<1, 4>(L, st);
-        case 16: return launch_update_t<1, 6>(L, st);
-        case 21: return launch_update_t<2, 1>(L, st);
-        case 23: return launch_update_t<2, 3>(L, st);
-        case 24: return launch_update_t<2, 4>(L, st);
-        case 41: return launch_update_t<4, 1>(L, st);
-        case 42: return launch_update_t<4, 2>(L, st);
-        case 43: return launch_update_t<4, 3>(L, st);
+        case 11: *c = pick(update_kernel<1, 1, false>, smem); return cudaSuccess;
+        case 14: *c = pick(update_kernel<1, 4, false>, smem); return cudaSuccess;
+        case 16: *c = pick(update_kernel<1, 6, false>, smem); return cudaSuccess;
+        case 21: *c = pick(update_kernel<2, 1, false>, smem); return cudaSuccess;
+        case 23: *c = pick(update_kernel<2, 3, false>, smem); return cudaSuccess;
+        case 24: *c = pick(update_kernel<2, 4, false>, smem); return cudaSuccess;
+        case 41: *c = pick(update_kernel<4, 1, false>, smem); return cudaSuccess;
+        case 42: *c = pick(update_kernel<4, 2, false>, smem); return cudaSuccess;
+        case 43: *c = pick(update_kernel<4, 3, false>, smem); return cudaSuccess;
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_update(const UpdateLaunch& L, cudaStream_t st) {
+    if (L.n_updates == 0) return cudaSuccess;
+    UpdateKernelChoice c;
+    cudaError_t e = choose_update_kernel(L, &c);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(c.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+    if (e != cudaSuccess) return e;
+    void* args[] = {const_cast<UpdateLaunch*>(&L)};
+    return cudaLaunchKernel(c.fn, dim3((unsigned)L.grid), dim3((unsigned)L.block), args, c.smem, st);
+}
+
+int update_blocks_per_sm(const UpdateLaunch& L) {
+    UpdateKernelChoice c;
+    int nb = 0;
+    if (choose_update_kernel(L, &c) != cudaSuccess) return 0;
+    if (cudaFuncSetAttribute(c.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, c.fn, L.block, c.smem) != cudaSuccess) return 0;
+    return nb;
 }
 
 cudaError_t launch_debug_sample_reuse(const SamplerArgs& s, uint32_t R, uint64_t n_sel, uint64_t q_begin,
