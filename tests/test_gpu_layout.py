@@ -89,9 +89,9 @@ def test_layout_stress_matches_oracle(pg, name):
       spread (reading R29);
     - the chromosome graph (one seed, each oracle run takes hours): five GPU
       repeats against the oracle's repeats of the same seed; SE from the
-      measured run-to-run spreads of both; bar max(1 %, 2 SE). It needs two
-      oracle runs at least, else the oracle's spread is unknown and the test
-      skips."""
+      measured run-to-run spreads of both; bar max(1 %, 2 SE), and it must
+      resolve the target (2 SE <= 1 %). It needs two oracle runs at least,
+      else the oracle's spread is unknown and the test skips."""
     gold = _gold(name)
     g = make_graph(gold.get("graph", name))
     fp = gold["fingerprint"]
@@ -111,7 +111,7 @@ def test_layout_stress_matches_oracle(pg, name):
         se = np.sqrt(got.var(ddof=1) / len(got) + ref.var(ddof=1) / len(ref))
     bar = max(0.01 * ref.mean(), 2 * se)
     print(name, got, ref, (got.mean() - ref.mean()) / ref.mean(), 2 * se / ref.mean())
-    if name == "mid_1000":
+    if name in ("mid_1000", "chrom"):  # these records resolve the target: the bar is the 1 % itself
         assert 2 * se <= 0.01 * ref.mean(), (se, ref.mean())
     assert abs(got.mean() - ref.mean()) <= bar, (got, ref, bar)
     assert got.max() < 0.5 * gold["init_stress"]
