@@ -297,7 +297,11 @@ def stress_vs_oracle(G, config):
     path = os.path.join(ROOT, "tests", "golden", "oracle_layouts.json")
     if not os.path.exists(path):
         return None
-    rec = json.load(open(path)).get(config)
+    data = json.load(open(path))
+    # prefer the record with the larger sample set where there is one (reading: the
+    # 200 k-node graph's stress at 100 samples per step is dominated by its sample set)
+    name = f"{config}_1000" if f"{config}_1000" in data else config
+    rec = data.get(name)
     if not rec:
         return None
     runs = [r for r in rec["runs"] if r["seed"] == SEED]
@@ -305,7 +309,7 @@ def stress_vs_oracle(G, config):
         return None
     st = G.stress(rec["stress_samples_per_step"], seed=rec["stress_seed"])
     ref = np.array([r["stress"] for r in runs])
-    out = {"samples_per_step": rec["stress_samples_per_step"], "stress_seed": rec["stress_seed"],
+    out = {"record": name, "samples_per_step": rec["stress_samples_per_step"], "stress_seed": rec["stress_seed"],
            "layout_seed": SEED, "gpu_mean": st["mean"], "gpu_ci": [st["ci_lo"], st["ci_hi"]],
            "oracle_mean": float(ref.mean()), "oracle_runs": len(ref), "oracle_threads": rec["oracle_threads"],
            "oracle_ci_first_run": [runs[0]["ci_lo"], runs[0]["ci_hi"]],
