@@ -224,6 +224,17 @@ def make_workload(config):
     return make_graph(config)
 
 
+def workload_config(name, n_nodes, n_paths, n_steps, ws):
+    """The `config` object of both arms' lines: the workload and its sizes
+    (the same for the GPU arm and the oracle arm), and how L2 is handled
+    between timed steps: the 16-byte step records alone exceed L2, so no flush."""
+    return {"workload": WORKLOADS[name], "name": name, "n_nodes": int(n_nodes), "n_paths": int(n_paths),
+            "n_steps": int(n_steps), "iterations": ITERS, "updates_per_step": ITERS * 10 * int(n_steps),
+            "stress_samples_per_step": STRESS_PER_STEP * int(n_steps),
+            "l2": f"inputs larger than L2 ({16 * n_steps / 1e9:.1f} GB of step records), no flush",
+            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"}
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -341,10 +352,10 @@ def run_reference(args):
         "ms_per_step": updates_per_step / value * 1e3, "higher_is_better": True,
         "ms_per_step_extrapolated": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.config], "name": args.config,
-                   "sample": "each step times bounded samples of a mixed (t = 2) and a cooling (t = 20) "
-                             "iteration (see cpu_baseline); ms_per_step is one whole layout's updates at "
-                             "that rate, extrapolated, not timed"},
+        "config": workload_config(args.config, g.n_nodes, g.n_paths, g.n_steps, args.gpus),
+        "sample": "each step times bounded samples of a mixed (t = 2) and a cooling (t = 20) "
+                  "iteration (see cpu_baseline); ms_per_step is one whole layout's updates at "
+                  "that rate, extrapolated, not timed",
         "cpu_baseline": cb,
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -474,12 +485,8 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.config], "name": args.config,
-                       "n_nodes": info["n_nodes"], "n_paths": info["n_paths"], "n_steps": S,
-                       "iterations": ITERS, "updates_per_step": updates_per_step,
-                       "stress_samples_per_step": STRESS_PER_STEP * S,
-                       "l2": f"inputs larger than L2 ({info['device_bytes'] / 1e9:.1f} GB resident), no flush",
-                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "config": workload_config(args.config, info["n_nodes"], info["n_paths"], S, ws),
+            "device_bytes": info["device_bytes"],
             "stress": {"mean": st["mean"], "ci_lo": st["ci_lo"], "ci_hi": st["ci_hi"],
                        "n_valid": st["n_valid"]},
             "layout_only_updates_per_s": upd / (upd_ms / 1e3) if upd_ms > 0 else None,

@@ -31,6 +31,9 @@ def test_reference_arm_prints_one_line_of_the_contract():
     from synth import make_graph
     S = make_graph("tiny").n_steps
     assert d["ms_per_step"] == pytest.approx(30 * 10 * S / d["value"] * 1e3, rel=1e-9)
+    # the same workload object as the GPU arm's line (sizes included)
+    g = make_graph("tiny")
+    assert d["config"] == bench.workload_config("tiny", g.n_nodes, g.n_paths, g.n_steps, 1)
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "updates/s", "h2d_bytes_per_step": 0,

@@ -53,15 +53,17 @@ def test_linear_path_converges_on_gpu(pg):
 
 
 def test_tiny_layout_quality_matches_oracle_within_1_percent(pg):
-    """The 1 % target resolved: 40 layout seeds on each side (the oracle
+    """The 1 % target resolved: 64 layout seeds on each side (the oracle
     sequential, the GPU lock-free, each seed's draws the same on both), so
     that two standard errors of the difference of the means, from the
     measured seed-to-seed spreads, come below 1 % of the oracle's mean; the
-    bar is then 1 %."""
+    bar is then 1 %. (With 40 seeds 2 SE came to 0.90-0.95 %, too close to
+    the 1 % it must stay under for a sample variance of 40 lock-free runs;
+    64 seeds put it near 0.7 %.)"""
     g = make_graph("tiny")
     ref = []
     got = []
-    for seed in range(1, 41):
+    for seed in range(1, 65):
         xy, _ = O.layout(g, g.init_xy, T=T, theta=0.99, seed=seed)
         ref.append(O.sampled_stress(g, xy, seed=7)["mean"])
         got.append(_layout_stress(pg, g, seed, 100, 7)[0]["mean"])
