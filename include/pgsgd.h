@@ -82,12 +82,18 @@ typedef enum pgsgd_option {
     /* Concurrency cap: the update kernel's grid is shrunk so that at most this
      * many updates are in flight at once, where the resident blocks would
      * otherwise hold more (0 = no cap; -1, the default,
-     * = max(2048, n_nodes / 4)). Small graphs under a full GB300 grid would
-     * otherwise see many simultaneous updates per node: on the 200 k-node
-     * graph a cap of n_nodes / 2 left the sampled stress 1.1 % above the
-     * oracle's (16 seeds, paired), n_nodes / 4 0.4 %, at 1.8x the layout
-     * time; on the 5.5 M-node graph the resident threads, not the cap, bound
-     * the updates in flight. */
+     * = max(64, n_nodes / 16, N / 5120) for N = PGSGD_OPT_UPDATES_PER_STEP x
+     * path steps updates per iteration). A cap below one block's worth also
+     * shrinks the block (whole warps, at least 64 threads) and, with the
+     * automatic shape, keeps 1 update per thread below 128. Concurrent
+     * updates read points that others are about to move and overwrite each
+     * other's moves; measured against the sequential oracle (paired by seed):
+     * 1-12 k-node graphs of 4-12 paths came out 3.4 % above its sampled
+     * stress with 2048 in flight and 0.26 % at n_nodes / 16; 1-4 k-node
+     * graphs of 50-90 paths 1.95 % with 2048, 0.19 % at N / 5120; the
+     * 200 k-node graph 0.4 % at n_nodes / 4 and 0.3 % at n_nodes / 16 (3.9x
+     * the layout time). On the 5.5 M-node graph the resident threads, not
+     * the cap, bound the updates in flight. */
     PGSGD_OPT_MAX_CONCURRENT = 9,
     /* Register budget of the update kernel: the number of resident 256-thread
      * blocks per SM its registers must allow (1 = compiler's choice; the

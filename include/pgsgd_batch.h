@@ -51,8 +51,11 @@ typedef enum pgsgd_batch_option {
     /* Updates per chunk, 1..2^31 (default 16384). */
     PGSGD_BOPT_CHUNK = 5,
     /* Per-graph cap on updates in flight: graph g runs at most
-     * max(1, cap / (block * updates per thread)) chunks at once.
-     * -1 (default) = max(2048, nodes of g / 4), the single-graph rule;
+     * max(1, cap / (block * updates per thread)) chunks at once; a cap
+     * below one block's worth runs one chunk at a time on the block's first
+     * max(32, cap / updates per thread) threads, rounded down to whole warps.
+     * -1 (default) = max(64, nodes of g / 16, updates of g per iteration
+     * / 5120), the single-graph rule;
      * 0 = no cap. */
     PGSGD_BOPT_MAX_CONCURRENT = 6,
     /* Updates per iteration of graph g = this value times its steps
@@ -173,13 +176,16 @@ int pgsgd_batch_timing_read(pgsgd_batch *b, double *total_ms, uint64_t *launches
  * n_updates[g] updates per iteration and n_nodes[g] nodes, rank_to_graph[G]
  * receives the order in which mode 0 lays out lanes and mode 1 scans queues
  * (most updates first, ties by graph index), n_chunks[g] the chunks per
- * iteration and lanes[g] the chunks graph g may run at once (0 for a graph
- * without updates). Arguments as the options of the same names.
+ * iteration, lanes[g] the chunks graph g may run at once (0 for a graph
+ * without updates) and threads[g] the threads of a block that run graph
+ * g's chunks (a multiple of 32, at most block). All seven arrays are host
+ * arrays of n_graphs entries owned by the caller. Arguments as the options
+ * of the same names.
  */
 int pgsgd_batch_plan(uint32_t n_graphs, const uint64_t *n_updates, const uint64_t *n_nodes,
                      int block, int updates_per_thread, uint64_t chunk,
                      int64_t max_concurrent, uint32_t *rank_to_graph,
-                     uint32_t *n_chunks, uint32_t *lanes);
+                     uint32_t *n_chunks, uint32_t *lanes, uint32_t *threads);
 
 #ifdef __cplusplus
 }

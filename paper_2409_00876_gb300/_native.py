@@ -79,7 +79,7 @@ _SIGS = {
     "pgsgd_batch_stress": ([P, u32, u64, P, P], i32),
     "pgsgd_batch_debug_sample": ([P, u32, u32, u32, dbl, u64, u64, u64, P, P], i32),
     "pgsgd_batch_timing_read": ([P, P, P, P, i32], i32),
-    "pgsgd_batch_plan": ([u32, P, P, i32, i32, u64, i64, P, P, P], i32),
+    "pgsgd_batch_plan": ([u32, P, P, i32, i32, u64, i64, P, P, P, P], i32),
     "pgsgd_l2_bandwidth": ([u64, u32, i32, P, P], i32),
     "pgsgd_hbm_gather_bandwidth": ([u64, u32, i32, i32, P, P], i32),
     "pgsgd_last_error": ([], C.c_char_p),

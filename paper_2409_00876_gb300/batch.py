@@ -24,7 +24,7 @@ def _u64p(a):
 
 
 def plan(n_updates, n_nodes, block=256, updates_per_thread=2, chunk=16384, max_concurrent=-1):
-    """Host-only schedule plan: (rank_to_graph, n_chunks, lanes)."""
+    """Host-only schedule plan: (rank_to_graph, n_chunks, lanes, threads)."""
     lib = N.load()
     nu = np.ascontiguousarray(n_updates, dtype=np.uint64)
     nn = np.ascontiguousarray(n_nodes, dtype=np.uint64)
@@ -32,9 +32,10 @@ def plan(n_updates, n_nodes, block=256, updates_per_thread=2, chunk=16384, max_c
     r2g = np.zeros(G, np.uint32)
     nch = np.zeros(G, np.uint32)
     lanes = np.zeros(G, np.uint32)
+    thr = np.zeros(G, np.uint32)
     N.check(lib.pgsgd_batch_plan(G, _u64p(nu), _u64p(nn), int(block), int(updates_per_thread), int(chunk),
-                                 int(max_concurrent), _u64p(r2g), _u64p(nch), _u64p(lanes)))
-    return r2g, nch, lanes
+                                 int(max_concurrent), _u64p(r2g), _u64p(nch), _u64p(lanes), _u64p(thr)))
+    return r2g, nch, lanes, thr
 
 
 class Batch:

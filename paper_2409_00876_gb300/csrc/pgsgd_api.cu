@@ -585,7 +585,12 @@ int pgsgd_layout(pgsgd_graph* g, uint32_t iter_max, const double* eta, double et
         return fail(PGSGD_EINVAL, "warp merging and data reuse run the plain update loop: set pipeline 0");
     const bool async_loop = g->async_depth > 0 && plain;
     const int pipe = g->pipeline >= 0 ? g->pipeline : (plain && !async_loop ? 1 : 0);
-    const int upt = g->upt > 0 ? g->upt : (pipe ? 2 : 1);
+    // concurrency cap: at most `cap` updates in flight (0 = none)
+    int64_t cap = g->max_concurrent;
+    if (cap == -1) cap = (int64_t)default_in_flight_cap(g->n_nodes, (uint64_t)g->updates_per_step * g->n_steps);
+    // the automatic shape keeps 1 update per thread where 2 would put a
+    // 64-thread block above the cap
+    const int upt = g->upt > 0 ? g->upt : (pipe && !(cap > 0 && cap < 128) ? 2 : 1);
     if (async_loop && (pipe || upt != 1))
         return fail(PGSGD_EINVAL, "the asynchronous step-record loop runs one update per thread: set pipeline 0 "
                                   "and updates_per_thread 1");
@@ -598,7 +603,12 @@ int pgsgd_layout(pgsgd_graph* g, uint32_t iter_max, const double* eta, double et
     L.nodes = g->d_nodes;
     L.u_begin = 0;
     L.n_updates = N;
+    // a cap below one block's worth shrinks the block (whole warps, at least
+    // 64 threads) before the grid is cut to the cap
+    const int64_t per_thread = g->drf > 1 ? g->drf : upt;
     L.block = g->block;
+    if (cap > 0 && cap < (int64_t)g->block * per_thread)
+        L.block = (int)std::max<int64_t>(64, cap / per_thread / 32 * 32);
     L.upt = upt;
     // automatic register budget for the plain loop: 4 resident blocks per SM
     // at 1 update per thread, 3 at 2 (no spills either way), else the
@@ -618,11 +628,9 @@ int pgsgd_layout(pgsgd_graph* g, uint32_t iter_max, const double* eta, double et
     // the resident blocks hold (a large graph keeps the full grid, whose
     // resident blocks hold fewer updates than the cap)
     int grid = g->sm_count * g->blocks_per_sm;
-    int64_t cap = g->max_concurrent;
-    if (cap == -1) cap = std::max<int64_t>(2048, (int64_t)g->n_nodes / 4);
     if (cap > 0) {
         // the cap counts updates: a thread keeps upt updates, or one selection of drf updates, in flight
-        const int64_t per_block = (int64_t)g->block * (g->drf > 1 ? g->drf : upt);
+        const int64_t per_block = (int64_t)L.block * per_thread;
         const int64_t gmax = std::max<int64_t>(1, cap / per_block);
         const int nb = update_blocks_per_sm(L);
         const int64_t resident = (int64_t)nb * g->sm_count;

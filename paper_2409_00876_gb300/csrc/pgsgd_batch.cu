@@ -18,9 +18,11 @@
 //           Waits for claimable work are bounded by a wall-clock budget and
 //           end in PGSGD_ETIMEOUT;
 //   mode 2  the comparison point: per iteration, one launch per graph.
-// Per graph at most `max_active` chunks are in flight, i.e. at most
-// max_active * block * upt updates at once (default cap max(2048, V_g / 4)
-// updates, the single-graph kernel's rule), so small graphs see no more
+// Per graph at most `max_active` chunks are in flight, each run by `threads`
+// threads of its block, i.e. at most max_active * threads * upt updates at
+// once (default cap max(64, V_g / 16, N_g / 5120) updates, the single-graph
+// kernel's rule): a graph whose cap is below one block's worth runs one
+// chunk at a time on part of the block, so small graphs see no more
 // simultaneous updates than when laid out alone.
 #include <algorithm>
 #include <cstdarg>
@@ -47,8 +49,10 @@ struct BatchGraph {
     uint32_t n_chunks;    // ceil(N_g / chunk)
     uint32_t max_active;  // chunks in flight at most (persistent) = lanes (launch modes)
     uint32_t key0, key1;  // Philox key = the graph's seed
+    uint32_t threads;     // threads of a block that run the graph's chunks (a multiple of 32)
+    uint32_t pad[3];
 };
-static_assert(sizeof(BatchGraph) == 48, "BatchGraph layout");
+static_assert(sizeof(BatchGraph) == 64, "BatchGraph layout");
 
 struct BatchLaunch {
     const BatchGraph* graphs;  // [G] rank order
@@ -137,7 +141,7 @@ __device__ __forceinline__ void stage_graph(const BatchLaunch& L, const BatchGra
 __device__ __forceinline__ BatchGraph load_graph(const BatchGraph* p) {
     BatchGraph G;
     const uint4* q = reinterpret_cast<const uint4*>(p);
-    const uint4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
+    const uint4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), d = __ldg(q + 3);
     G.step0 = (uint64_t)a.x | ((uint64_t)a.y << 32);
     G.n_steps = (uint64_t)a.z | ((uint64_t)a.w << 32);
     G.n_updates = (uint64_t)b.x | ((uint64_t)b.y << 32);
@@ -147,6 +151,7 @@ __device__ __forceinline__ BatchGraph load_graph(const BatchGraph* p) {
     G.max_active = c.y;
     G.key0 = c.z;
     G.key1 = c.w;
+    G.threads = d.x;
     return G;
 }
 
@@ -171,7 +176,8 @@ __device__ __forceinline__ SamplerArgs graph_sampler(const BatchLaunch& L, const
 }
 
 // The updates [c * chunk, min((c + 1) * chunk, N_g)) of iteration t of the
-// graph of rank r, by the whole block.
+// graph of rank r, by the block's first G.threads threads (the caller skips
+// the others; whole warps, so every warp runs or idles as one).
 template <int UPT, bool PIPE>
 __device__ __forceinline__ void run_chunk(const BatchLaunch& L, const BatchGraph& G, uint32_t r, const BatchSmem& s,
                                           const ZipfConsts& zc, uint32_t t, uint32_t c, uint64_t pol_stream,
@@ -182,10 +188,10 @@ __device__ __forceinline__ void run_chunk(const BatchLaunch& L, const BatchGraph
     const uint64_t cb = (uint64_t)c * L.chunk;
     const uint64_t ce = min(cb + L.chunk, G.n_updates);
     if (PIPE) {
-        update_range_pipelined<UPT>(a, pt, L.nodes, cb + threadIdx.x, blockDim.x, ce, o, pol_stream, pol_keep);
+        update_range_pipelined<UPT>(a, pt, L.nodes, cb + threadIdx.x, G.threads, ce, o, pol_stream, pol_keep);
     } else {
-        for (uint64_t base = cb + threadIdx.x; base < ce; base += (uint64_t)blockDim.x * UPT)
-            update_trip<UPT>(a, pt, L.nodes, base, blockDim.x, ce, o, pol_stream, pol_keep);
+        for (uint64_t base = cb + threadIdx.x; base < ce; base += (uint64_t)G.threads * UPT)
+            update_trip<UPT>(a, pt, L.nodes, base, G.threads, ce, o, pol_stream, pol_keep);
     }
 }
 
@@ -205,6 +211,7 @@ __global__ void __launch_bounds__(256) batch_lane_kernel(BatchLaunch L, uint32_t
     __syncthreads();
     const uint64_t pol_stream = policy_evict_first(), pol_keep = policy_evict_last();
     const uint32_t stride = G.max_active;
+    if (threadIdx.x >= G.threads) return;  // no barrier follows
     for (uint32_t c = ln.y; c < G.n_chunks; c += stride)
         run_chunk<UPT, PIPE>(L, G, ln.x, s, zc, t, c, pol_stream, pol_keep);
 }
@@ -340,7 +347,7 @@ __global__ void __launch_bounds__(256, UPT == 4 ? 2 : 3) batch_persistent_kernel
                 __syncthreads();
                 cur = r;
             }
-            run_chunk<UPT, PIPE>(L, G, r, s, zc, t, c, pol_stream, pol_keep);
+            if (threadIdx.x < G.threads) run_chunk<UPT, PIPE>(L, G, r, s, zc, t, c, pol_stream, pol_keep);
             __threadfence();
         }
         uint32_t next[4] = {0u, 0u, 0u, 0u};
@@ -613,7 +620,8 @@ void free_batch(pgsgd_batch* b) {
 // Plan shared by pgsgd_batch_plan and the layout: rank order (most updates
 // first, ties by graph index), chunks and in-flight chunk cap per graph.
 int make_plan(uint32_t G, const uint64_t* n_updates, const uint64_t* n_nodes, int block, int upt, uint64_t chunk,
-              int64_t max_concurrent, uint32_t* rank_to_graph, uint32_t* n_chunks, uint32_t* lanes) {
+              int64_t max_concurrent, uint32_t* rank_to_graph, uint32_t* n_chunks, uint32_t* lanes,
+              uint32_t* threads) {
     if (block < 64 || block > 256 || block % 32) return fail(PGSGD_EINVAL, "block %d not in 64..256 step 32", block);
     if (upt != 1 && upt != 2 && upt != 4) return fail(PGSGD_EINVAL, "updates per thread %d not 1, 2 or 4", upt);
     if (chunk == 0 || chunk > (1ull << 31)) return fail(PGSGD_EINVAL, "chunk %llu not in 1..2^31",
@@ -631,15 +639,19 @@ int make_plan(uint32_t G, const uint64_t* n_updates, const uint64_t* n_nodes, in
                                                (unsigned long long)nc);
         n_chunks[gi] = (uint32_t)nc;
         uint64_t active;
+        uint32_t thr = (uint32_t)block;
         if (max_concurrent == 0) {
             active = nc;
         } else {
             const uint64_t cap = max_concurrent > 0 ? (uint64_t)max_concurrent
-                                                    : std::max<uint64_t>(2048, n_nodes[gi] / 4);
+                                                    : default_in_flight_cap(n_nodes[gi], n_updates[gi]);
             active = std::max<uint64_t>(1, cap / per_block);
+            // below one block's worth: one chunk at a time on whole warps of the block
+            if (cap < per_block) thr = (uint32_t)std::max<uint64_t>(32, cap / (uint64_t)upt / 32 * 32);
         }
         lanes[gi] = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(active, 1), std::max<uint64_t>(nc, 1));
         if (nc == 0) lanes[gi] = 0;
+        threads[gi] = thr;
     }
     return PGSGD_OK;
 }
@@ -735,11 +747,11 @@ extern "C" {
 
 int pgsgd_batch_plan(uint32_t n_graphs, const uint64_t* n_updates, const uint64_t* n_nodes, int block, int upt,
                      uint64_t chunk, int64_t max_concurrent, uint32_t* rank_to_graph, uint32_t* n_chunks,
-                     uint32_t* lanes) {
-    if (n_graphs && (!n_updates || !n_nodes || !rank_to_graph || !n_chunks || !lanes))
+                     uint32_t* lanes, uint32_t* threads) {
+    if (n_graphs && (!n_updates || !n_nodes || !rank_to_graph || !n_chunks || !lanes || !threads))
         return fail(PGSGD_EINVAL, "NULL argument");
     return make_plan(n_graphs, n_updates, n_nodes, block, upt, chunk, max_concurrent, rank_to_graph, n_chunks,
-                     lanes);
+                     lanes, threads);
 }
 
 int pgsgd_batch_create(uint32_t n_graphs, const uint64_t* graph_node_off, const uint64_t* graph_path_off,
@@ -998,9 +1010,9 @@ int prepare(pgsgd_batch* b, const uint64_t* seeds, cudaStream_t st) {
         nu[k] = (uint64_t)b->updates_per_step * b->n_steps[k];
         nn[k] = b->node_off[k + 1] - b->node_off[k];
     }
-    std::vector<uint32_t> r2g(G), nch(G), lanes(G);
+    std::vector<uint32_t> r2g(G), nch(G), lanes(G), thr(G);
     int rc = make_plan(G, nu.data(), nn.data(), b->block, b->upt, (uint64_t)b->chunk, b->max_concurrent, r2g.data(),
-                       nch.data(), lanes.data());
+                       nch.data(), lanes.data(), thr.data());
     if (rc) return rc;
     b->rank_to_graph = r2g;
     b->plan.assign(G, BatchGraph{});
@@ -1015,6 +1027,7 @@ int prepare(pgsgd_batch* b, const uint64_t* seeds, cudaStream_t st) {
         x.n_updates = nu[k];
         x.n_chunks = nch[k];
         x.max_active = lanes[k];
+        x.threads = thr[k];
         x.key0 = (uint32_t)seeds[k];
         x.key1 = (uint32_t)(seeds[k] >> 32);
         b->lane_start[r + 1] = b->lane_start[r] + lanes[k];

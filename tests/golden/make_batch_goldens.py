@@ -1,8 +1,14 @@
 """Write the CPU oracle's per-graph layout quality for the batch workloads:
 
 - tests/golden/oracle_batch_small.json: every graph of the small batch
-  workload (12 graphs, 1 k - 12 k nodes, 4 - 12 paths), layout seeds 1-3,
-  one thread (the sequential reading of the method);
+  workload (12 graphs, 1 k - 12 k nodes, 4 - 12 paths), layout seeds 1-128,
+  one thread (the sequential reading of the method); single layouts of
+  1 k-node graphs vary by tens of percent from seed to seed, so the
+  comparison needs this many seeds to resolve a few percent;
+- tests/golden/oracle_batch_highpath.json: four small graphs of the
+  256-subgraph workload with many paths per node (1.1 k - 3.9 k nodes,
+  65 - 88 paths), layout seeds 1-16, one thread: the graphs where many
+  updates meet few nodes;
 - tests/golden/oracle_batch256_subset.json: a fixed subset of 16 graphs of
   the 256-subgraph workload spanning its size range (the graphs at 16 evenly
   spaced ranks 0..240 of 256 by size), each under the layout
@@ -14,7 +20,7 @@ from the generator's initial layout and records the sampled path stress
 (Eq. 2) of the result under a fixed stress seed. Only the oracle and the
 input generator are called; graphs run in parallel worker processes.
 
-    python tests/golden/make_batch_goldens.py [--workload batch_small|batch256] [--workers 4]
+    python tests/golden/make_batch_goldens.py [--workload batch_small|highpath|batch256] [--workers 4]
 """
 import argparse
 import hashlib
@@ -34,7 +40,10 @@ T = 30
 THETA = 0.99
 PER_STEP = 100
 STRESS_SEED = 7
-SMALL_SEEDS = [1, 2, 3]
+SMALL_SEEDS = list(range(1, 129))
+SEED_CHUNK = 16              # seeds per worker job (the small record)
+HIGHPATH_INDICES = [73, 52, 21, 80]  # batch256 graphs of 1,097, 1,336, 2,951 and 3,928 nodes, 65-88 paths
+HIGHPATH_SEEDS = list(range(1, 17))
 SUBSET_SIZE = 16
 SUBSET_TOP_RANK = 240       # ranks 0..240 of 256 by step count: the largest graphs stay out (CPU time)
 THREADED_ABOVE = 1_000_000  # steps; larger subset graphs use Hogwild! threads
@@ -71,7 +80,7 @@ def _one(job):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="batch_small", choices=["batch_small", "batch256"])
+    ap.add_argument("--workload", default="batch_small", choices=["batch_small", "batch256", "highpath"])
     ap.add_argument("--workers", type=int, default=4)
     args = ap.parse_args()
     from synth import BATCH_CONFIGS
@@ -79,8 +88,14 @@ def main():
     sha = hashlib.sha1(strip_comments(open(os.path.join(ROOT, "oracle", "pgsgd_oracle.c")).read()).encode()).hexdigest()[:12]
     if args.workload == "batch_small":
         idx = list(range(BATCH_CONFIGS["batch_small"]["n_graphs"]))
-        jobs = [("batch_small", k, SMALL_SEEDS, 1) for k in idx]
+        jobs = [("batch_small", k, SMALL_SEEDS[c:c + SEED_CHUNK], 1) for k in idx
+                for c in range(0, len(SMALL_SEEDS), SEED_CHUNK)]
         out = os.path.join(HERE, "oracle_batch_small.json")
+    elif args.workload == "highpath":
+        idx = HIGHPATH_INDICES
+        jobs = [("batch256", k, HIGHPATH_SEEDS[c:c + SEED_CHUNK // 4], 1) for k in idx
+                for c in range(0, len(HIGHPATH_SEEDS), SEED_CHUNK // 4)]
+        out = os.path.join(HERE, "oracle_batch_highpath.json")
     else:
         idx = subset_indices()
         jobs = [("batch256", k, [k + 1], None) for k in idx]
@@ -88,11 +103,22 @@ def main():
     recs = {}
     with mp.get_context("spawn").Pool(args.workers) as pool:
         for k, rec in pool.imap_unordered(_one, jobs):
-            recs[k] = rec
-            print(k, rec, flush=True)
+            if k in recs:  # another chunk of this graph's seeds
+                have = recs[k]
+                pairs = sorted(zip(have["seeds"] + rec["seeds"], have["stress"] + rec["stress"]))
+                have["seeds"], have["stress"] = [a for a, _ in pairs], [b for _, b in pairs]
+                have["seconds"] = round(have["seconds"] + rec["seconds"], 1)
+            else:
+                recs[k] = rec
+            print(k, rec["seeds"][0], len(rec["seeds"]), rec["seconds"], flush=True)
     graphs = [recs[k] for k in idx]
     data = dict(workload=args.workload, oracle_sha=sha, iterations=T, theta=THETA, updates_per_step=10,
                 stress_samples_per_step=PER_STEP, stress_seed=STRESS_SEED, graphs=graphs)
+    if args.workload == "highpath":
+        data["source_workload"] = "batch256"
+        data["seeds"] = HIGHPATH_SEEDS
+        for g in graphs:
+            g.pop("oracle_threads")
     if args.workload == "batch_small":
         data["seeds"] = SMALL_SEEDS
         for g in graphs:  # the small record keeps its original per-graph fields

@@ -47,25 +47,31 @@ def _plan(*a, **k):
 def test_plan_orders_by_work_and_caps_lanes():
     nu = np.array([100, 0, 5000, 5000, 70000], np.uint64)
     nn = np.array([10, 5, 4000, 100000, 3000], np.uint64)
-    r2g, nch, lanes = _plan(nu, nn, block=256, updates_per_thread=2, chunk=1000)
+    r2g, nch, lanes, thr = _plan(nu, nn, block=256, updates_per_thread=2, chunk=1000)
     # most updates first, ties by graph index
     assert list(r2g) == [4, 2, 3, 0, 1]
     np.testing.assert_array_equal(nch, [1, 0, 5, 5, 70])
-    # cap = max(2048, V / 4) updates in flight = cap // 512 chunks, at most the chunks there are
-    caps = np.maximum(2048, nn // 4) // 512
-    np.testing.assert_array_equal(lanes, np.where(nch == 0, 0, np.minimum(np.maximum(caps, 1), nch)))
+    # cap = max(64, V / 16, N / 5120) updates in flight = cap // 512 chunks, at most the chunks there are
+    cap = np.maximum(64, np.maximum(nn // 16, nu // 5120))
+    np.testing.assert_array_equal(lanes, np.where(nch == 0, 0, np.minimum(np.maximum(cap // 512, 1), nch)))
+    # a cap below one block's worth (512 updates) runs on whole warps: max(32, cap / 2) rounded down to 32
+    np.testing.assert_array_equal(thr, np.where(cap < 512, np.maximum(32, cap // 2 // 32 * 32), 256))
+    assert list(thr) == [32, 32, 96, 256, 64]
 
 
 def test_plan_options_change_lanes():
     nu = np.array([10_000_000], np.uint64)
     nn = np.array([200_000], np.uint64)
-    _, nch, lanes = _plan(nu, nn, block=128, updates_per_thread=4, chunk=4096)
+    _, nch, lanes, thr = _plan(nu, nn, block=128, updates_per_thread=4, chunk=4096)
     assert nch[0] == -(-10_000_000 // 4096)
-    assert lanes[0] == 50_000 // 512  # cap V / 4 = 50,000 updates over 128 x 4 per lane
-    _, _, lanes0 = _plan(nu, nn, chunk=4096, max_concurrent=0)
-    assert lanes0[0] == nch[0]  # no cap: every chunk may run at once
-    _, _, lanes1 = _plan(nu, nn, chunk=4096, max_concurrent=100)
-    assert lanes1[0] == 1
+    assert lanes[0] == 12_500 // 512 and thr[0] == 128  # cap V / 16 = 12,500 updates over 128 x 4 per lane
+    _, _, lanes0, thr0 = _plan(nu, nn, chunk=4096, max_concurrent=0)
+    assert lanes0[0] == nch[0] and thr0[0] == 256  # no cap: every chunk may run at once on whole blocks
+    _, _, lanes1, thr1 = _plan(nu, nn, chunk=4096, max_concurrent=100)
+    assert lanes1[0] == 1 and thr1[0] == 32  # 100 updates at 2 per thread: one warp
+    # many updates per node: the N / 5120 term sets the cap (10 M / 5120 = 1953 > 1000 / 16)
+    _, _, lanes2, thr2 = _plan(nu, [1000], chunk=4096)
+    assert lanes2[0] == 1953 // 512 and thr2[0] == 256
 
 
 @pytest.mark.parametrize("kw", [dict(block=48), dict(block=288), dict(updates_per_thread=3), dict(chunk=0),

@@ -23,6 +23,7 @@ pytestmark = pytest.mark.gpu
 T = 30
 THETA = 0.99
 GOLD = os.path.join(os.path.dirname(__file__), "golden", "oracle_batch_small.json")
+HIGHPATH = os.path.join(os.path.dirname(__file__), "golden", "oracle_batch_highpath.json")
 FIELDS = ["g", "i", "j", "d_ref", "path", "cooling", "e_i", "e_j", "skip"]
 
 
@@ -99,33 +100,79 @@ def _gold():
 
 @pytest.mark.parametrize("mode", [0, 1, 2])
 def test_layout_quality_matches_oracle(small, mode):
-    """Per graph, the mean stress over the recorded layout seeds, GPU batch
-    against the oracle; pooled over graphs the ratio must be within 1 % or
-    three standard errors of the seed-to-seed spread, and no graph may be
-    far off."""
+    """Per graph and layout seed, the GPU batch's sampled stress against the
+    oracle's for that graph alone under the same seed (the same draws on both
+    sides; reading R28). Single layouts of these 1 k - 12 k-node graphs vary by
+    tens of percent from seed to seed (some seeds fold a graph into a layout
+    of several times the typical stress), so the record holds 128 seeds per
+    graph and the comparison is paired by seed: per graph the mean of the
+    per-seed differences relative to the oracle's mean, pooled over the 12
+    graphs with SE from the measured spread of the per-seed differences. The
+    pooled difference must lie within max(1 %, 2 SE), the comparison must
+    resolve the 1 % target (2 SE <= 1 %), and no graph may be far off. The
+    benchmarked schedule (mode 0) runs the first 64 seeds, the persistent
+    kernel 32 and one launch per graph (the slowest schedule) 16."""
     gold = _gold()
     gs, arr, B = small
     for k, g in enumerate(gs):
         rec = gold["graphs"][k]
         assert (g.n_nodes, g.n_paths, g.n_steps) == (rec["n_nodes"], rec["n_paths"], rec["n_steps"])
     B.set_option("mode", mode)
+    n_seeds = {0: 64, 1: 32, 2: 16}[mode]
+    runs = []
+    for s in gold["seeds"][:n_seeds]:
+        B.set_coords(arr.init_xy)
+        B.layout(gold["iterations"], seeds=s, theta=gold["theta"])
+        runs.append([r["mean"] for r in B.stress(gold["stress_samples_per_step"], gold["stress_seed"])])
+    got = np.array(runs).T                                   # [G, seeds]
+    ref = np.array([r["stress"][:n_seeds] for r in gold["graphs"]])  # [G, seeds]
+    n = got.shape[1]
+    rel = (got - ref) / ref.mean(axis=1, keepdims=True)      # paired, relative to the oracle's mean
+    per_graph = rel.mean(axis=1)
+    se_graph = rel.std(axis=1, ddof=1) / np.sqrt(n)
+    pooled = per_graph.mean()
+    se = np.sqrt(np.sum(se_graph ** 2)) / len(per_graph)
+    corr = [np.corrcoef(got[k], ref[k])[0, 1] for k in range(len(gs))]
+    print("mode", mode, "per-graph differences", np.round(per_graph, 4), "2 SE", np.round(2 * se_graph, 4),
+          "seed correlation", np.round(corr, 2), "pooled", pooled, "2 SE", 2 * se)
+    assert 2 * se <= 0.01, se                                # the comparison resolves 1 %
+    assert abs(pooled) <= max(0.01, 2 * se), (pooled, se)
+    # a graph the schedule broke would sit far from the oracle or near its initial stress
+    assert np.all(np.abs(per_graph) <= np.maximum(0.15, 4 * se_graph)), (per_graph, se_graph)
+    init = np.array([r["init_stress"] for r in gold["graphs"]])
+    assert np.all(got.mean(axis=1) < init)
+
+
+def test_many_paths_per_node_quality_matches_oracle():
+    """Small graphs with many paths per node (1.1-3.9 k nodes, 65-88 paths,
+    from the 256-subgraph workload): each node receives hundreds of moves per
+    iteration, and the cap's N / 5120 term lets more updates run at once
+    than n_nodes / 16 would. Laid out together in one batch (mode 0) under
+    16 layout seeds, paired by seed with the oracle's layouts of each graph
+    alone: the pooled relative difference within max(1 %, 2 SE), the
+    comparison resolving 1 % (2 SE <= 1 %). With 2048 updates in flight
+    these graphs came out 1.95 % above the oracle."""
+    from paper_2409_00876_gb300.batch import Batch
+    gold = json.load(open(HIGHPATH))
+    gs = make_batch(gold["source_workload"], indices=[r["index"] for r in gold["graphs"]])
+    for g, rec in zip(gs, gold["graphs"]):
+        assert (g.n_nodes, g.n_paths, g.n_steps) == (rec["n_nodes"], rec["n_paths"], rec["n_steps"])
+    arr = concat(gs)
+    B = Batch.from_arrays(arr)
     runs = []
     for s in gold["seeds"]:
         B.set_coords(arr.init_xy)
         B.layout(gold["iterations"], seeds=s, theta=gold["theta"])
         runs.append([r["mean"] for r in B.stress(gold["stress_samples_per_step"], gold["stress_seed"])])
-    got = np.array(runs).T                                   # [G, seeds]
-    ref = np.array([r["stress"] for r in gold["graphs"]])    # [G, seeds]
-    ratio = got.mean(axis=1) / ref.mean(axis=1)
-    n = got.shape[1]
-    rel_var = got.var(axis=1, ddof=1) / got.mean(axis=1) ** 2 / n + ref.var(axis=1, ddof=1) / ref.mean(axis=1) ** 2 / n
-    se = np.sqrt(rel_var.sum()) / len(ratio)
-    print("mode", mode, "ratios", np.round(ratio, 4), "mean", ratio.mean(), "se", se)
-    assert abs(ratio.mean() - 1) <= max(0.01, 3 * se), (ratio, se)
-    # a graph the schedule broke would sit near or above its initial stress
-    assert np.all(ratio < 1.5) and np.all(ratio > 0.67), ratio
-    init = np.array([r["init_stress"] for r in gold["graphs"]])
-    assert np.all(got.mean(axis=1) < init)
+    B.close()
+    got = np.array(runs).T
+    ref = np.array([r["stress"] for r in gold["graphs"]])
+    rel = (got - ref) / ref.mean(axis=1, keepdims=True)
+    per_graph = rel.mean(axis=1)
+    se = np.sqrt(np.sum(rel.var(axis=1, ddof=1) / rel.shape[1])) / len(per_graph)
+    print("many paths: per-graph differences", np.round(per_graph, 4), "pooled", per_graph.mean(), "2 SE", 2 * se)
+    assert 2 * se <= 0.01, se
+    assert abs(per_graph.mean()) <= max(0.01, 2 * se), (per_graph, se)
 
 
 def test_modes_launch_counts_and_graph_replay(small):

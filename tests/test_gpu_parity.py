@@ -229,6 +229,53 @@ def test_graph_from_device_tensors_matches_host(pg):
     _compare_samples(Gd.debug_sample(3, T, THETA, 1, 0, 50_000), Gh.debug_sample(3, T, THETA, 1, 0, 50_000))
 
 
+# ------------------------------------------------------------------ largest positions
+
+def _long_graph(grow=0):
+    """Nodes of about 2^30 nt, so that step positions come within a few nt of
+    2^32 (the limit of the 32-bit position field) and reference distances pass
+    2^31: a signed 32-bit step anywhere in the position arithmetic shows.
+    ``grow`` lengthens node 3 and pushes the later positions past the limit."""
+    big = (1 << 30) - 1
+    lens = [big, big, big, big - 10 + grow, 5, 7, 3]
+    paths = [[(0, 0), (1, 0), (2, 1), (3, 0), (4, 0), (5, 1)],
+             [(6, 0), (3, 1), (1, 0), (4, 1), (6, 1)],
+             [(2, 0), (4, 0), (5, 0), (6, 0)]]
+    rng = np.random.Generator(np.random.PCG64(5))
+    xy = rng.uniform(-1e6, 1e6, size=(len(lens), 4)).astype(np.float32).astype(np.float64)
+    return make_custom(lens, paths, init_xy=xy)
+
+
+def test_positions_near_2_32_stay_exact(pg):
+    g = _long_graph()
+    last = int(g.step_pos[5]) + int(g.node_len[5])
+    assert (1 << 32) - 16 < last < (1 << 32)
+    G = _gpu_graph(pg, g)
+    n = 20_000
+    for t in (0, 20):
+        got = G.debug_sample(t, T, THETA, 3, 0, n)
+        want = O.sample(g, T, t, THETA, 3, 0, n)
+        _compare_samples(got, want)
+        assert int(want["d_ref"].max()) > (1 << 31)
+    xy = G.get_coords()
+    eta = O.eta_schedule(T, O.default_eta_max(g))
+    for t in (0, 29):
+        _sweep_check(G, g, xy, t, eta[t], 3, 0, n)
+    got = G.stress(100, seed=11, per_path=True)
+    want = O.sampled_stress(g, xy, per_step=100, seed=11, per_path=True)
+    assert got["n_valid"] == want["n_valid"] and got["n_skipped"] == want["n_skipped"]
+    assert abs(got["mean"] - want["mean"]) <= 1e-4 * want["mean"]
+    np.testing.assert_array_equal(got["per_path"][:, 2], want["per_path"][:, 2])
+
+
+def test_positions_at_2_32_are_a_range_error(pg):
+    from paper_2409_00876_gb300 import PgsgdError
+    g = _long_graph(grow=15)
+    assert int(g.step_pos.max()) >= (1 << 32)
+    with pytest.raises(PgsgdError, match="2\\^32"):
+        pg.Graph.from_synth(g)
+
+
 # ------------------------------------------------------------------ full-size, sampled
 
 @pytest.fixture(scope="module")
