@@ -62,6 +62,18 @@ def test_too_many_paths_is_a_range_error(lib):
     assert h.value is None
 
 
+def test_too_many_nodes_is_a_range_error(lib):
+    # node ids are packed into 31 bits of the step record; the count is
+    # refused before any array is read
+    one = np.ones(1, np.uint32)
+    off = np.zeros(2, np.uint64)
+    h = C.c_void_p()
+    rc = lib.pgsgd_create(one.ctypes.data_as(C.c_void_p), 1 << 31, off.ctypes.data_as(C.c_void_p), 1,
+                          None, None, None, 0, None, C.byref(h))
+    assert rc == N.PGSGD_ERANGE and h.value is None
+    assert "2^31" in lib.pgsgd_last_error().decode()
+
+
 def test_null_output_handle(lib):
     one = np.ones(1, np.uint32)
     off = np.zeros(2, np.uint64)
