@@ -175,7 +175,8 @@ int pgsgd_batch_timing_read(pgsgd_batch *b, double *total_ms, uint64_t *launches
  * The schedule plan, on the host only (no GPU needed): for G graphs with
  * n_updates[g] updates per iteration and n_nodes[g] nodes, rank_to_graph[G]
  * receives the order in which mode 0 lays out lanes and mode 1 scans queues
- * (most updates first, ties by graph index), n_chunks[g] the chunks per
+ * (the graphs whose lanes run the most sequential rounds of updates
+ * first, ties by most updates, then graph index), n_chunks[g] the chunks per
  * iteration, lanes[g] the chunks graph g may run at once (0 for a graph
  * without updates) and threads[g] the threads of a block that run graph
  * g's chunks (a multiple of 32, at most block). All seven arrays are host

@@ -224,7 +224,7 @@ __device__ __forceinline__ bool can_claim(unsigned long long qv, uint32_t n_chun
     return it < iter_end && nx < n_chunks && nx - done < cap;
 }
 
-// Warp 0: claim one chunk, scanning graphs in rank order (largest first).
+// Warp 0: claim one chunk, scanning graphs in rank order (longest lanes first).
 // Returns 0 = claimed (r, t, c), 1 = nothing claimable now, 2 = all graphs
 // finished, 3 = error raised.
 __device__ int claim_chunk(const BatchLaunch& L, const BatchQueues& Q, uint32_t& r, uint32_t& t, uint32_t& c) {
@@ -617,8 +617,13 @@ void free_batch(pgsgd_batch* b) {
     delete b;
 }
 
-// Plan shared by pgsgd_batch_plan and the layout: rank order (most updates
-// first, ties by graph index), chunks and in-flight chunk cap per graph.
+// Plan shared by pgsgd_batch_plan and the layout: chunks, in-flight chunk cap
+// and threads per lane of every graph, and the rank order: the longest lanes
+// first (a lane's sequential rounds of updates: its updates, at most
+// ceil(chunks / lanes) chunks, over threads x upt), ties by most updates, then
+// graph index, so
+// that the lanes a concurrency cap makes long start in the first wave instead
+// of extending the iteration at its end.
 int make_plan(uint32_t G, const uint64_t* n_updates, const uint64_t* n_nodes, int block, int upt, uint64_t chunk,
               int64_t max_concurrent, uint32_t* rank_to_graph, uint32_t* n_chunks, uint32_t* lanes,
               uint32_t* threads) {
@@ -627,12 +632,7 @@ int make_plan(uint32_t G, const uint64_t* n_updates, const uint64_t* n_nodes, in
     if (chunk == 0 || chunk > (1ull << 31)) return fail(PGSGD_EINVAL, "chunk %llu not in 1..2^31",
                                                         (unsigned long long)chunk);
     if (max_concurrent < -1) return fail(PGSGD_EINVAL, "max_concurrent %lld < -1", (long long)max_concurrent);
-    std::vector<uint32_t> order(G);
-    std::iota(order.begin(), order.end(), 0u);
-    std::stable_sort(order.begin(), order.end(),
-                     [&](uint32_t a, uint32_t b) { return n_updates[a] > n_updates[b]; });
     const uint64_t per_block = (uint64_t)block * upt;
-    for (uint32_t r = 0; r < G; ++r) rank_to_graph[r] = order[r];
     for (uint32_t gi = 0; gi < G; ++gi) {
         const uint64_t nc = (n_updates[gi] + chunk - 1) / chunk;
         if (nc >= (1ull << 32) - 1) return fail(PGSGD_ERANGE, "graph %u: %llu chunks per iteration", gi,
@@ -653,6 +653,19 @@ int make_plan(uint32_t G, const uint64_t* n_updates, const uint64_t* n_nodes, in
         if (nc == 0) lanes[gi] = 0;
         threads[gi] = thr;
     }
+    std::vector<uint64_t> rounds(G, 0);
+    for (uint32_t gi = 0; gi < G; ++gi) {
+        if (!lanes[gi]) continue;
+        const uint64_t per_trip = (uint64_t)threads[gi] * upt;
+        const uint64_t per_lane = std::min<uint64_t>(n_updates[gi], (n_chunks[gi] + lanes[gi] - 1) / lanes[gi] * chunk);
+        rounds[gi] = (per_lane + per_trip - 1) / per_trip;
+    }
+    std::vector<uint32_t> order(G);
+    std::iota(order.begin(), order.end(), 0u);
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) {
+        return rounds[a] != rounds[b] ? rounds[a] > rounds[b] : n_updates[a] > n_updates[b];
+    });
+    for (uint32_t r = 0; r < G; ++r) rank_to_graph[r] = order[r];
     return PGSGD_OK;
 }
 

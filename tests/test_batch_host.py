@@ -48,7 +48,7 @@ def test_plan_orders_by_work_and_caps_lanes():
     nu = np.array([100, 0, 5000, 5000, 70000], np.uint64)
     nn = np.array([10, 5, 4000, 100000, 3000], np.uint64)
     r2g, nch, lanes, thr = _plan(nu, nn, block=256, updates_per_thread=2, chunk=1000)
-    # most updates first, ties by graph index
+    # longest lanes first (rounds 547, 27, then 2 and 2 broken by most updates, then 0)
     assert list(r2g) == [4, 2, 3, 0, 1]
     np.testing.assert_array_equal(nch, [1, 0, 5, 5, 70])
     # cap = max(64, V / 16, N / 5120) updates in flight = cap // 512 chunks, at most the chunks there are
@@ -57,6 +57,16 @@ def test_plan_orders_by_work_and_caps_lanes():
     # a cap below one block's worth (512 updates) runs on whole warps: max(32, cap / 2) rounded down to 32
     np.testing.assert_array_equal(thr, np.where(cap < 512, np.maximum(32, cap // 2 // 32 * 32), 256))
     assert list(thr) == [32, 32, 96, 256, 64]
+
+
+def test_plan_starts_the_longest_lanes_first():
+    # a small graph with many paths per node runs one lane of 5,209 rounds
+    # (cap 1 M / 5120 = 195 updates: 96 threads x 2); the large graph 122
+    # lanes of 160 rounds: the small graph ranks first despite fewer updates
+    r2g, nch, lanes, thr = _plan(np.array([10_000_000, 1_000_000], np.uint64),
+                                 np.array([1_000_000, 1_000], np.uint64))
+    assert list(lanes) == [122, 1] and list(thr) == [256, 96]
+    assert list(r2g) == [1, 0]
 
 
 def test_plan_options_change_lanes():

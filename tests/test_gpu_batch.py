@@ -347,7 +347,7 @@ def test_full_batch_in_the_benchmarked_schedule():
 
 @pytest.mark.parametrize("mode", [0, 1, 2])
 def test_per_graph_learning_rates_reach_their_graphs(mode):
-    """Graphs are scheduled in rank order (most updates first); the caller's
+    """Graphs are scheduled in rank order (longest lanes first); the caller's
     per-graph eta rows must still reach the right graphs: a graph given
     eta = 0 in every iteration keeps its layout exactly, the others move."""
     from paper_2409_00876_gb300.batch import Batch
