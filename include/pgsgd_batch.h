@@ -179,7 +179,7 @@ int pgsgd_batch_timing_read(pgsgd_batch *b, double *total_ms, uint64_t *launches
  * first, ties by most updates, then graph index), n_chunks[g] the chunks per
  * iteration, lanes[g] the chunks graph g may run at once (0 for a graph
  * without updates) and threads[g] the threads of a block that run graph
- * g's chunks (a multiple of 32, at most block). All seven arrays are host
+ * g's chunks (a multiple of 32, at most block). All six arrays are host
  * arrays of n_graphs entries owned by the caller. Arguments as the options
  * of the same names.
  */
