@@ -117,3 +117,36 @@ def test_random_gather_fields_of_the_roofline():
     assert r["frac_of_random_gather"] == pytest.approx(42.9 / 48)
     assert r["gather_reference"]["update_frac"] == pytest.approx(21.4 / 22)
     assert r["frac"] == pytest.approx(4100.0 / 6785.2)
+
+
+def test_sampled_schedule_timing_scales_to_the_whole_layout():
+    """The one-graph-at-a-time schedules are timed over the iterations of
+    SAMPLED_ITERATIONS and scaled to ITERS; the rate is the timed updates over
+    the timed milliseconds."""
+    calls = []
+
+    class FakeBatch:
+        def __init__(self):
+            self.pending = None
+
+        def set_coords(self, xy):
+            pass
+
+        def set_option(self, k, v):
+            pass
+
+        def timing_read(self, reset=False):
+            out, self.pending = self.pending, None
+            return out if out else (0.0, 0, 0)
+
+        def layout(self, iter_max, seeds=None, theta=None, iter_begin=0, iter_end=None):
+            calls.append((iter_begin, iter_end))
+            n = iter_end - iter_begin
+            self.pending = (10.0 * n, 3 * n, 1_000_000 * n)  # ms, launches, updates per timed call
+
+    out = bench._batch_sampled(FakeBatch(), None, None)
+    its = sum(b - a for a, b in bench.SAMPLED_ITERATIONS)
+    assert calls == [tuple(x) for x in bench.SAMPLED_ITERATIONS]
+    assert out["timed_ms"] == 10.0 * its and out["ms"] == pytest.approx(10.0 * bench.ITERS)
+    assert out["updates_per_s"] == pytest.approx(1e6 * its / (10.0 * its / 1e3))
+    assert out["launches"] == 3 * bench.ITERS and out["ms_extrapolated"] is True
