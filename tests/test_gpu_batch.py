@@ -109,16 +109,18 @@ def test_layout_quality_matches_oracle(small, mode):
     per-seed differences relative to the oracle's mean, pooled over the 12
     graphs with SE from the measured spread of the per-seed differences. The
     pooled difference must lie within max(1 %, 2 SE), the comparison must
-    resolve the 1 % target (2 SE <= 1 %), and no graph may be far off. The
-    benchmarked schedule (mode 0) runs the first 64 seeds, the persistent
-    kernel 32 and one launch per graph (the slowest schedule) 16."""
+    resolve the 1 % target (2 SE <= 1 %), and no graph may be far off. Every
+    schedule runs the first 64 seeds: one graph (5 k nodes) folds on about
+    one seed in ten into a layout of three times the typical stress, and a
+    seed that folds on one side only moves its mean by several percent, which
+    16 seeds did not dilute enough (2 SE 1.2 % in two runs)."""
     gold = _gold()
     gs, arr, B = small
     for k, g in enumerate(gs):
         rec = gold["graphs"][k]
         assert (g.n_nodes, g.n_paths, g.n_steps) == (rec["n_nodes"], rec["n_paths"], rec["n_steps"])
     B.set_option("mode", mode)
-    n_seeds = {0: 64, 1: 32, 2: 16}[mode]
+    n_seeds = 64
     runs = []
     for s in gold["seeds"][:n_seeds]:
         B.set_coords(arr.init_xy)
