@@ -621,9 +621,8 @@ void free_batch(pgsgd_batch* b) {
 // and threads per lane of every graph, and the rank order: the longest lanes
 // first (a lane's sequential rounds of updates: its updates, at most
 // ceil(chunks / lanes) chunks, over threads x upt), ties by most updates, then
-// graph index, so
-// that the lanes a concurrency cap makes long start in the first wave instead
-// of extending the iteration at its end.
+// graph index, so that the lanes a concurrency cap makes long start in the
+// first wave instead of extending the iteration at its end.
 int make_plan(uint32_t G, const uint64_t* n_updates, const uint64_t* n_nodes, int block, int upt, uint64_t chunk,
               int64_t max_concurrent, uint32_t* rank_to_graph, uint32_t* n_chunks, uint32_t* lanes,
               uint32_t* threads) {
